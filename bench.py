@@ -1,0 +1,360 @@
+#!/usr/bin/env python
+"""Benchmark: spin updates per ns of the Trotter-Suzuki Monte Carlo on GB300.
+
+One step is one pass of the whole hot path over the workload: for the default
+workload (128 samples, L=24, L_tau=2048, 4 replicas, 32 k in [0.22, 0.36],
+heat bath) it is 10 elementary steps of the paper's Methods -- 30 sweeps and
+one parallel-tempering attempt each -- followed by one measurement of the
+imaginary-time correlators: 300 sweeps, 10 tempering steps, 1 measurement.
+The metric counts attempted spin updates (every site of every sample, replica
+and k, once per sweep).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank simulates its own disorder samples (weak
+scaling, no collective on the data path); the timed region is bracketed by a
+barrier and a device synchronisation and the maximum over ranks is reported.
+``--impl reference`` times the plain CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+SWEEP_BYTES_PER_WORD = 16  # read + write of every site word once per sweep
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="L24_Lt2048_hb")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# profile-derived DRAM traffic of the sweep kernel (null once the kernel changed)
+# ---------------------------------------------------------------------------
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2310_07486_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.startswith("k_sweep") or fn.startswith("k_wavefront") or fn == "qsg_device.cuh":
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload):
+    path = os.path.join(ROOT, "profiles", "sweep_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_hash") != kernel_source_hash() or d.get("workload") != workload:
+        return None
+    return d.get("dram_bytes_per_sweep")
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def step_plan(w):
+    """(sweeps per tempering step, tempering steps per step, measurements per step)."""
+    n_swaps = max(1, w.measure_every // w.sweeps_per_swap)
+    return w.sweeps_per_swap, n_swaps, 1
+
+
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    from paper_2310_07486_gb300 import qsg as Q
+    from paper_2310_07486_gb300 import workloads
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    w = workloads.ALL[args.workload]()
+    seed = w.seed + 1000003 * rank  # each rank simulates its own samples
+    stream = torch.cuda.current_stream()
+    ctx = Q.Context(w.shapes, device=torch.device("cuda", local), stream=stream)
+    ctx.qsg_init_samples(seed, w.ladders)
+    sps, nswap, nmeas = step_plan(w)
+    updates_per_step = w.spin_updates_per_sweep * sps * nswap
+
+    sweep_events = []
+
+    def one_step(record):
+        for _ in range(nswap):
+            if record:
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+            ctx.qsg_sweep(sps)
+            if record:
+                b.record(stream)
+                sweep_events.append((a, b))
+            ctx.qsg_tempering_swap()
+        ctx.qsg_measure_correlators()
+
+    for _ in range(args.warmup):
+        one_step(False)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = Q.qsg_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        one_step(True)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    launches = Q.qsg_kernel_launches() - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = t0.elapsed_time(t1) / args.steps
+    sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_events) / (len(sweep_events) * sps)
+    if dist:
+        tt = torch.tensor([ms, sweep_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms, sweep_ms = float(tt[0]), float(tt[1])
+    value = updates_per_step * world / (ms * 1e6)
+
+    # end to end through the C ABI with host buffers: the state is uploaded
+    # from pinned host memory, the step runs, the correlators come back
+    e2e = None
+    if not args.no_e2e:
+        host_states = []
+        h2d = 0
+        for gi, s in enumerate(w.shapes):
+            words = ctx.qsg_get_spins(gi)
+            pinned = torch.from_numpy(words.view(np.int64)).pin_memory()
+            host_states.append(pinned)
+            h2d += words.nbytes
+        d2h = sum(2 * s.n_replicas * s.n_samples * s.n_k * s.n_lag * 8 + s.n_samples * s.n_k * 8 for s in w.shapes)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        for _ in range(args.steps):
+            for gi, hs in enumerate(host_states):
+                ctx.qsg_set_spins(gi, hs.numpy().view(np.uint64))
+            one_step(False)
+            for gi in range(len(w.shapes)):
+                ctx.qsg_read_correlators(gi)
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t_start) * 1e3 / args.steps
+        if dist:
+            tt = torch.tensor([e2e_ms], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_ms = float(tt[0])
+        e2e = {"value": updates_per_step * world / (e2e_ms * 1e6), "unit": "spin-flips/ns",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peak_kind = load_peaks()
+    words = w.words
+    achieved = SWEEP_BYTES_PER_WORD * words / (sweep_ms * 1e-3) / 1e9
+    traffic = profiled_traffic(w.name)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": "qsg_sweep (one full sweep)",
+                "algorithmic_bytes_per_launch": SWEEP_BYTES_PER_WORD * words, "peak_kind": peak_kind,
+                "launch_ms": sweep_ms, "spin_flips_per_ns_sweep_only": w.spin_updates_per_sweep / (sweep_ms * 1e6)}
+    out = {
+        "metric": "spin-flips/ns", "value": value, "unit": "spin-flips/ns", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": w.name,
+                   "shapes": [dict(L=s.L, Ltau=s.Ltau, samples=s.n_samples, replicas=s.n_replicas, n_k=s.n_k,
+                                   algo="heatbath" if s.algo else "metropolis",
+                                   boundary="apbc" if s.boundary else "pbc") for s in w.shapes],
+                   "step": {"sweeps": sps * nswap, "tempering_steps": nswap, "measurements": nmeas},
+                   "spin_updates_per_step": updates_per_step, "state_bytes": 8 * words,
+                   "l2": "inputs larger than L2 (state %.2f GB)" % (8 * words / 1e9),
+                   "parallelism": "replicas-only x%d" % world},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": e2e,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle timings (host cores)
+# ---------------------------------------------------------------------------
+def oracle_subset(w, n_k, R=None):
+    import oracle
+    s, lad = w.shapes[0], w.ladders[0]
+    R = R or s.n_replicas
+    g = oracle.OracleGroup(s.L, s.Ltau, 1, R, n_k, algo=s.algo, boundary=s.boundary)
+    g.init(w.seed, lad[:n_k])
+    return g, s
+
+
+def cpu_baseline(w):
+    """The oracle on one sample, 4 replicas x 4 k values (16 configurations):
+    one sweep, one tempering step and one measurement of all 16 configurations,
+    timed and scaled to the full step (per configuration-sweep and
+    configuration-measurement)."""
+    g, s = oracle_subset(w, 4)
+    configs = g.n_samples * g.R * g.K
+    t = time.perf_counter()
+    g.sweep(1)
+    t_sweep = (time.perf_counter() - t) / configs
+    t = time.perf_counter()
+    g.swap()
+    t_swap = (time.perf_counter() - t) / configs
+    t = time.perf_counter()
+    g.measure()
+    t_meas = (time.perf_counter() - t) / configs
+    sps, nswap, nmeas = step_plan(w)
+    full_configs = sum(x.n_samples * x.n_replicas * x.n_k for x in w.shapes)
+    t_step = full_configs * (t_sweep * sps * nswap + t_swap * nswap + t_meas * nmeas)
+    updates = w.spin_updates_per_sweep * sps * nswap
+    return {"value": updates / (t_step * 1e9), "unit": "spin-flips/ns", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "1 sample x %d replicas x %d k (L=%d, L_tau=%d): 1 sweep, 1 tempering step, 1 measurement "
+                      "timed, scaled per configuration to the full step" % (g.R, g.K, s.L, s.Ltau),
+            "seconds_per_config_sweep": t_sweep, "seconds_per_config_measure": t_meas}
+
+
+def run_reference(args, rank, world, local):
+    """The plain CPU oracle: each step = 30 sweeps of 1 sample x 4 replicas x
+    2 k values, one tempering step and the correlators of one configuration
+    (the same sweep : measurement mix as a full step)."""
+    if rank != 0:
+        return
+    from paper_2310_07486_gb300 import workloads
+    w = workloads.ALL[args.workload]()
+    g, s = oracle_subset(w, 2)
+    sweeps = 30
+    updates = s.L * s.L * s.Ltau * g.R * g.K * sweeps
+
+    def step():
+        g.sweep(sweeps)
+        g.swap()
+        g.measure_one(0, 0, 0)
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    ms = (time.perf_counter() - t) * 1e3 / args.steps
+    value = updates / (ms * 1e6)
+    sample = "1 sample x %d replicas x %d k of %s: %d sweeps, 1 tempering step, 1 configuration's correlators" % (
+        g.R, g.K, w.name, sweeps)
+    out = {"impl": "reference", "metric": "spin-flips/ns", "value": value, "unit": "spin-flips/ns", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+           "config": {"workload": w.name, "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "spin-flips/ns", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "spin-flips/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world, local)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

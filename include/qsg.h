@@ -1,0 +1,169 @@
+/*
+ * qsg.h -- C ABI of the GB300 (sm_103a) Monte Carlo library for the
+ * Trotter-Suzuki representation of the two-dimensional +-1 Ising spin glass
+ * in a transverse field (arXiv 2310.07486, "The Quantum Transition of the
+ * Two-Dimensional Ising Spin Glass: A Tale of Two Gaps").
+ *
+ * Model (Methods, Eq. (Trotter-action) and Eq. (P-S-tau)): classical spins
+ * S_{x,tau} = +-1 on an L x L x L_tau lattice, periodic in space, periodic
+ * (PBC) or antiperiodic (APBC, only along tau) in imaginary time, with weight
+ * exp(-k E(S)) and action
+ *     E(S) = - sum_tau [ sum_<x,y> J_xy S_x,tau S_y,tau + sum_x S_x,tau S_x,tau+1 ].
+ * Space bonds carry k J_xy and time bonds k; the transverse field of Eq. (H-def)
+ * is Gamma = -ln(tanh k) / (2k).  Couplings J_xy = +-1 with probability 1/2
+ * (Methods, "Model and simulations").
+ *
+ * Storage (multispin coding): spins of 64 disorder samples share one uint64
+ * word; bit b of word w is sample 64 w + b and a set bit means S = -1.  A
+ * "slot" is one lattice of L*L*L_tau words for the word-group w, replica r and
+ * ladder position j, slot = (w * R + r) * K + j, words ordered [tau][y][x].
+ * Parallel tempering moves spin bits between the slots of one (w, r), so the
+ * lattice in slot (w, r, j) is always simulated at k_j.
+ *
+ * Randomness: Philox4x32-10 (Salmon et al., SC'11) keyed by the 64-bit seed
+ * (low word first).  Counters, with gid the group index:
+ *   couplings   (n = y L + x, dir, w, 1<<24 | gid<<8): bits of out[0] | out[1]<<32
+ *   hot start   (n, 0, slot, 2<<24 | gid<<8):           bits of out[0] | out[1]<<32
+ *   sweep       (block, sweep, slot, 3<<24 | gid<<8): site (x, y, tau) takes
+ *               out[(tau & 1) * 2 + (x & 1)] with block = ((tau/2) L + y)(L/2) + x/2;
+ *               one 32-bit uniform per site, sweep and slot, shared by the 64
+ *               samples of the word
+ *   tempering   (16 i + b/4, swap index, w R + r, 4<<24 | gid<<8): sample bit b
+ *               of pair i takes out[b & 3]
+ *
+ * Acceptance is an integer comparison u < T against 32-bit tables built on the
+ * host in FP64 (Methods, "Simulation details"):
+ *   Metropolis  flip iff S h <= 0 or u < floor(2^32 exp(-(2 k (S h))))
+ *   heat bath   S = +1 iff u < min(floor(2^32 / (1 + exp(-(2 k h)))), 2^32 - 1)
+ *   tempering   pairs i = 0 .. K-2 in order; swap iff E_{i+1} >= E_i or
+ *               u < (A_i[n >> 6] * B_i[n & 63]) >> 32, n = E_i - E_{i+1},
+ *               A_i[m] = floor(2^32 exp(-(d_i (64 m)))), B_i[r] = floor(2^32 exp(-(d_i r))),
+ *               d_i = k_{i+1} - k_i (uint64 product)
+ * where h = sum_space J S_nb + sum_time s S_nb (s = -1 on the APBC wrap bond).
+ *
+ * Conventions: every call returns a qsg_status and nothing is thrown across
+ * the ABI.  Device work is enqueued on the caller's CUDA stream; calls named
+ * read_* / get_* / set_* synchronise that stream, no other call does.  The
+ * library allocates no device memory: the caller passes one device workspace
+ * of qsg_workspace_bytes() bytes, owned by the caller and used by the library
+ * until qsg_destroy().  Host pointers passed to a call are read or written
+ * only during that call.
+ */
+#ifndef QSG_H
+#define QSG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsg_ctx qsg_ctx;
+
+typedef enum {
+    QSG_OK = 0,
+    QSG_ERR_ARG = -1,       /* null pointer, bad group index, bad ladder, bad count */
+    QSG_ERR_SHAPE = -2,     /* L or L_tau odd or out of range, counts < 1 */
+    QSG_ERR_CUDA = -3,      /* a CUDA runtime call failed (see qsg_last_cuda_error) */
+    QSG_ERR_TIMEOUT = -4,   /* a bounded device wait gave up; results are invalid */
+    QSG_ERR_STATE = -5,     /* call out of order (e.g. sweep before init) */
+    QSG_ERR_WORKSPACE = -6  /* workspace missing, misaligned or too small */
+} qsg_status;
+
+enum { QSG_METROPOLIS = 0, QSG_HEATBATH = 1 };
+enum { QSG_PBC = 0, QSG_APBC = 1 };
+
+/* One group of disorder samples that share (L, L_tau, R, K, algorithm,
+ * boundary).  Several groups of different sizes may live in one context. */
+typedef struct {
+    int32_t L;          /* linear size, even, 2 <= L <= 32 */
+    int32_t Ltau;       /* Trotter slices, even, 2 <= L_tau <= 65536 */
+    int32_t n_samples;  /* disorder samples, >= 1 (stored in ceil(n/64) words) */
+    int32_t n_replicas; /* independent replicas per sample and k, >= 1 */
+    int32_t n_k;        /* ladder length K, 1 <= K <= 128 */
+    int32_t algo;       /* QSG_METROPOLIS or QSG_HEATBATH */
+    int32_t boundary;   /* QSG_PBC or QSG_APBC (along tau only; Methods, Trotter-Suzuki) */
+    int32_t reserved;   /* must be 0 */
+} qsg_shape;
+
+/* Bytes of device workspace needed for these groups (0 on invalid shapes). */
+size_t qsg_workspace_bytes(const qsg_shape *shapes, int32_t n_groups);
+
+/* Create a context over a caller-owned device workspace (256-byte aligned,
+ * at least qsg_workspace_bytes() bytes) on CUDA stream `cuda_stream`
+ * (a cudaStream_t, may be NULL for the legacy default stream). */
+qsg_status qsg_create(qsg_ctx **out, const qsg_shape *shapes, int32_t n_groups, void *d_workspace,
+                      size_t workspace_bytes, void *cuda_stream);
+void qsg_destroy(qsg_ctx *ctx);
+qsg_status qsg_set_stream(qsg_ctx *ctx, void *cuda_stream);
+
+/* Draw the couplings J of every sample (Methods, "Model and simulations"),
+ * the hot-start configurations of every slot, build the acceptance tables
+ * from the k ladders and clear all accumulators and counters.
+ * k_ladders (host): for each group in order, n_k values 0 < k_0 < ... < k_{K-1} < 3. */
+qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders);
+
+/* Replace the couplings of one group (host int8 [n_samples][2][L][L] of +-1;
+ * [.][0][y][x] couples (x,y)-(x+1,y), [.][1][y][x] couples (x,y)-(x,y+1)).
+ * Clears the cached actions.  Synchronises the stream. */
+qsg_status qsg_set_couplings(qsg_ctx *ctx, int32_t group, const int8_t *J_host);
+
+/* n_sweeps full checkerboard sweeps of every slot of every group (Methods,
+ * "Simulation details"; colour (x+y+tau) mod 2, colour 0 then colour 1).
+ * Advances the sweep counter by n_sweeps. */
+qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps);
+
+/* One parallel-tempering step over the k ladder of every (sample, replica)
+ * (Methods, "Simulation details"), using the action of the current
+ * configurations.  Accepted swaps exchange the spin bits of that sample between
+ * the two slots.  Advances the swap counter. */
+qsg_status qsg_tempering_swap(qsg_ctx *ctx);
+
+/* Accumulate, in int64 on the device, for every slot and sample bit
+ *   C_acc[r][b][j][tau] += sum_tau1 s c(tau1, tau),  Q_acc[r][b][j][tau] += sum_tau1 c(tau1, tau)^2,
+ * c = sum_x S_x,tau1 S_x,tau1+tau (s = -1 when tau1+tau wraps under APBC), and
+ *   P_acc[b][j] += sum_{r<r'} sum_tau1 (sum_x S^r_x,tau1 S^r'_x,tau1)^2
+ * for tau = 0 .. L_tau/2 (Eqs. (C_A_transfer), (def-C-Q2-tau); the replica
+ * overlap is the Tr M^2 / L^2D comparator of the Q2 plateau). */
+qsg_status qsg_measure_correlators(qsg_ctx *ctx);
+
+/* FP64 finish of one group on the device (Eq. (def-C-Q2-tau)):
+ *   C = C_acc / (n_meas L^2 L_tau), Q2 = Q_acc / (n_meas L^4 L_tau),
+ *   q2 = P_acc / (n_meas n_pairs L^4 L_tau), n_pairs = R (R-1) / 2,
+ * then copied to host buffers C, Q2 [R][n_samples][K][L_tau/2+1] and
+ * q2 [n_samples][K] (any may be NULL).  raw (optional, host int64) receives
+ * C_acc then Q_acc then P_acc in the same layouts.  Synchronises the stream. */
+qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw);
+
+/* Action E of every configuration, host int64 [n_samples][R][K] (ladder
+ * position j).  Computes it if no sweep fused it.  Synchronises the stream. */
+qsg_status qsg_read_energies(qsg_ctx *ctx, int32_t group, int64_t *E_host);
+
+/* Accepted tempering swaps summed over replicas, host int64 [n_samples][K-1]. */
+qsg_status qsg_read_accepts(qsg_ctx *ctx, int32_t group, int64_t *acc_host);
+
+/* Spin words of one group, host uint64 [slots][L_tau][L][L] (checkpoint,
+ * tests).  set_spins also clears the cached actions.  Both synchronise. */
+qsg_status qsg_get_spins(qsg_ctx *ctx, int32_t group, uint64_t *host);
+qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host);
+
+/* Counters: sweeps done, tempering steps done, measurements accumulated.
+ * The sweep and swap counters key the Philox streams, so restoring them with
+ * the spins (and the couplings, re-drawn by qsg_init_samples from the same
+ * seed) resumes a run bit for bit.  n_meas < 0 leaves the measurement count. */
+qsg_status qsg_get_counters(qsg_ctx *ctx, uint32_t *sweeps, uint32_t *swaps, int64_t *n_meas);
+qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64_t n_meas);
+
+/* Number of kernels this library has launched in this process (all contexts);
+ * a diagnostic for benchmarks and for checking that the GPU path ran. */
+uint64_t qsg_kernel_launches(void);
+
+const char *qsg_strerror(qsg_status status);
+/* Text of the last CUDA error seen by this context (empty if none). */
+const char *qsg_last_cuda_error(qsg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSG_H */

@@ -47,7 +47,7 @@ def lib():
             vp, i32, u32, u64, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
             L.orc_philox.argtypes = [vp, vp, vp]
             L.orc_create.restype = vp
-            L.orc_create.argtypes = [i32] * 8
+            L.orc_create.argtypes = [i32] * 9
             L.orc_destroy.argtypes = [vp]
             L.orc_init.restype = i32
             L.orc_init.argtypes = [vp, u64, vp, i32, vp]
@@ -56,6 +56,7 @@ def lib():
             L.orc_swap.argtypes = [vp]
             L.orc_measure.argtypes = [vp]
             L.orc_read.argtypes = [vp] * 7
+            L.orc_measure_one.argtypes = [vp, i32, i32, i32, vp, vp]
             L.orc_get_spins.argtypes = [vp, vp]
             L.orc_set_spins.argtypes = [vp, vp]
             L.orc_get_couplings.argtypes = [vp, vp]
@@ -95,12 +96,15 @@ class OracleGroup:
       q2         float64 [n_samples][K]
     """
 
-    def __init__(self, L, Ltau, n_samples, n_replicas, n_k, algo="metropolis", boundary="pbc", group_id=0):
+    def __init__(self, L, Ltau, n_samples, n_replicas, n_k, algo="metropolis", boundary="pbc", group_id=0,
+                 first_sample=0):
         self.L, self.Ltau, self.n_samples, self.R, self.K = L, Ltau, n_samples, n_replicas, n_k
         self.algo = {"metropolis": 0, "heatbath": 1}[algo] if isinstance(algo, str) else int(algo)
         self.boundary = {"pbc": 0, "apbc": 1}[boundary] if isinstance(boundary, str) else int(boundary)
         self.group_id = group_id
-        self._h = lib().orc_create(L, Ltau, n_samples, n_replicas, n_k, self.algo, self.boundary, group_id)
+        self.first_sample = first_sample
+        self._h = lib().orc_create(L, Ltau, n_samples, n_replicas, n_k, self.algo, self.boundary, group_id,
+                                   first_sample)
         if not self._h:
             raise ValueError("oracle: invalid shape")
         self.n_lag = Ltau // 2 + 1
@@ -133,6 +137,12 @@ class OracleGroup:
 
     def measure(self):
         lib().orc_measure(self._h)
+
+    def measure_one(self, b, r, j):
+        C = np.zeros(self.n_lag, dtype=np.int64)
+        Q = np.zeros(self.n_lag, dtype=np.int64)
+        lib().orc_measure_one(self._h, b, r, j, _ptr(C), _ptr(Q))
+        return C, Q
 
     def read(self):
         shp = (self.R, self.n_samples, self.K, self.n_lag)

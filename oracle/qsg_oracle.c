@@ -94,6 +94,7 @@ static void draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t 
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int L, Ltau, n_samples, R, K, algo, boundary, group_id;
+    int first;      /* global index of local sample 0 (word (first+b)/64, bit (first+b)%64) */
     int N;          /* L*L*Ltau sites */
     int n_lag;      /* Ltau/2 + 1 */
     uint64_t seed;
@@ -125,20 +126,24 @@ static int8_t *config(orc_group *g, int b, int r, int j)
     return g->S + ((size_t)((size_t)b * g->R + r) * g->K + j) * (size_t)g->N;
 }
 
+/* global sample index of local sample b */
+static int gsample(const orc_group *g, int b) { return g->first + b; }
+
 /* slot index of (sample b, replica r, ladder position j): the multispin word
  * w = b / 64 holds 64 samples; each (w, r, j) owns one random stream. */
 static uint32_t slot_of(const orc_group *g, int b, int r, int j)
 {
-    return (uint32_t)((((b / 64) * g->R) + r) * g->K + j);
+    return (uint32_t)((((gsample(g, b) / 64) * g->R) + r) * g->K + j);
 }
 
-orc_group *orc_create(int L, int Ltau, int n_samples, int R, int K, int algo, int boundary, int group_id)
+/* n_samples samples with global indices first .. first+n_samples-1 */
+orc_group *orc_create(int L, int Ltau, int n_samples, int R, int K, int algo, int boundary, int group_id, int first)
 {
-    if (L < 2 || (L & 1) || Ltau < 2 || (Ltau & 1) || n_samples < 1 || R < 1 || K < 1)
+    if (L < 2 || (L & 1) || Ltau < 2 || (Ltau & 1) || n_samples < 1 || R < 1 || K < 1 || first < 0)
         return NULL;
     orc_group *g = (orc_group *)calloc(1, sizeof(orc_group));
     g->L = L; g->Ltau = Ltau; g->n_samples = n_samples; g->R = R; g->K = K;
-    g->algo = algo; g->boundary = boundary; g->group_id = group_id;
+    g->algo = algo; g->boundary = boundary; g->group_id = group_id; g->first = first;
     g->N = L * L * Ltau;
     g->n_lag = Ltau / 2 + 1;
     size_t ns = (size_t)n_samples;
@@ -252,9 +257,10 @@ int orc_init(orc_group *g, uint64_t seed, const double *ladders, int per_sample,
                     v = J_in[((size_t)b * 2 + d) * L * L + n];
                 } else {
                     uint32_t o[4];
-                    draw(seed, (uint32_t)n, (uint32_t)d, (uint32_t)(b / 64), (ORC_STREAM_J << 24) | tag, o);
+                    int gb = gsample(g, b);
+                    draw(seed, (uint32_t)n, (uint32_t)d, (uint32_t)(gb / 64), (ORC_STREAM_J << 24) | tag, o);
                     uint64_t bits = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
-                    v = ((bits >> (b % 64)) & 1u) ? -1 : 1;
+                    v = ((bits >> (gb % 64)) & 1u) ? -1 : 1;
                 }
                 g->J[((size_t)b * 2 + d) * L * L + n] = v;
             }
@@ -268,7 +274,7 @@ int orc_init(orc_group *g, uint64_t seed, const double *ladders, int per_sample,
                     uint32_t o[4];
                     draw(seed, (uint32_t)n, 0u, s, (ORC_STREAM_INIT << 24) | tag, o);
                     uint64_t bits = (uint64_t)o[0] | ((uint64_t)o[1] << 32);
-                    S[n] = ((bits >> (b % 64)) & 1u) ? -1 : 1;
+                    S[n] = ((bits >> (gsample(g, b) % 64)) & 1u) ? -1 : 1;
                 }
             }
     memset(g->Cacc, 0, sizeof(int64_t) * (size_t)g->R * g->n_samples * K * g->n_lag);
@@ -400,8 +406,9 @@ void orc_swap(orc_group *g)
             int64_t *E = g->E + ((size_t)b * g->R + r) * K;
             for (int i = 0; i + 1 < K; ++i) {
                 uint32_t o[4];
-                draw(g->seed, (uint32_t)(i * 16 + (b % 64) / 4), m, (uint32_t)((b / 64) * g->R + r), tag, o);
-                uint32_t u = o[(b % 64) & 3];
+                int gb = gsample(g, b);
+                draw(g->seed, (uint32_t)(i * 16 + (gb % 64) / 4), m, (uint32_t)((gb / 64) * g->R + r), tag, o);
+                uint32_t u = o[(gb % 64) & 3];
                 int accept;
                 if (E[i + 1] >= E[i]) {
                     accept = 1;
@@ -471,6 +478,27 @@ void orc_measure(orc_group *g)
         g->Pacc[c] += sum;
     }
     g->n_meas++;
+}
+
+/* Correlator sums of ONE configuration (sample b, replica r, ladder j), not
+ * accumulated: C_out[lag] = sum_tau1 s c, Q_out[lag] = sum_tau1 c^2. */
+void orc_measure_one(orc_group *g, int b, int r, int j, int64_t *C_out, int64_t *Q_out)
+{
+    int L2 = g->L * g->L, Lt = g->Ltau;
+    const int8_t *S = config(g, b, r, j);
+    for (int lag = 0; lag < g->n_lag; ++lag) {
+        int64_t csum = 0, qsum = 0;
+        for (int t1 = 0; t1 < Lt; ++t1) {
+            int t2 = t1 + lag, sgn = 1;
+            if (t2 >= Lt) { t2 -= Lt; if (g->boundary == 1) sgn = -1; }
+            int64_t cc = 0;
+            for (int xy = 0; xy < L2; ++xy) cc += S[t1 * L2 + xy] * S[t2 * L2 + xy];
+            csum += sgn * cc;
+            qsum += cc * cc;
+        }
+        C_out[lag] = csum;
+        Q_out[lag] = qsum;
+    }
 }
 
 /* FP64 finish: C = Cacc / (n_meas L^2 L_tau); Q2 = Qacc / (n_meas L^4 L_tau);

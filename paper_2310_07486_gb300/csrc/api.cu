@@ -1,0 +1,456 @@
+// api.cu -- host side of the C ABI declared in include/qsg.h: validation,
+// workspace carving, acceptance tables, and the ordering of kernel launches.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "qsg.h"
+#include "qsg_launch.h"
+
+using namespace qsg;
+
+static std::atomic<unsigned long long> g_launches{0};
+void qsg::count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxA = 16384;               // longest A_i table of the tempering test
+constexpr size_t kScratchCap = 256u << 20;  // bytes of transposed scratch for the correlators
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool valid_shape(const qsg_shape &s) {
+    if (s.L < 2 || s.L > 32 || (s.L & 1)) return false;
+    if (s.Ltau < 2 || s.Ltau > 65536 || (s.Ltau & 1)) return false;
+    if (s.n_samples < 1 || s.n_replicas < 1 || s.n_k < 1 || s.n_k > 128) return false;
+    if (s.algo != QSG_METROPOLIS && s.algo != QSG_HEATBATH) return false;
+    if (s.boundary != QSG_PBC && s.boundary != QSG_APBC) return false;
+    if (s.reserved != 0) return false;
+    const double words = (double)((s.n_samples + 63) / 64) * s.n_replicas * s.n_k * (double)s.L * s.L * s.Ltau;
+    return words < 4.0e10;
+}
+
+Group describe(const qsg_shape &s, int gid) {
+    Group g;
+    std::memset(&g, 0, sizeof(g));
+    g.L = s.L;
+    g.Ltau = s.Ltau;
+    g.W = (s.n_samples + 63) / 64;
+    g.R = s.n_replicas;
+    g.K = s.n_k;
+    g.algo = s.algo;
+    g.boundary = s.boundary;
+    g.gid = gid;
+    g.N = s.L * s.L * s.Ltau;
+    g.nslots = g.W * g.R * g.K;
+    g.nlag = s.Ltau / 2 + 1;
+    g.n_samples = s.n_samples;
+    g.nwx = (s.L * s.L + 63) / 64;
+    return g;
+}
+
+int a_cap(const Group &g) {
+    const long long need = (6LL * g.N >> 6) + 1;
+    return (int)(need < kMaxA ? need : kMaxA);
+}
+
+// Walk the workspace: when base is null only the size is computed.
+size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, size_t *scratch_words) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off = align_up(off + bytes);
+        return p;
+    };
+    *err = (int *)take(sizeof(int) * 4);
+    size_t sw = 0;
+    for (auto &g : gs) {
+        g.S = (uint64_t *)take(sizeof(uint64_t) * (size_t)g.nslots * g.N);
+        g.Jx = (uint64_t *)take(sizeof(uint64_t) * (size_t)g.W * g.L * g.L);
+        g.Jy = (uint64_t *)take(sizeof(uint64_t) * (size_t)g.W * g.L * g.L);
+        g.thr = (uint32_t *)take(sizeof(uint32_t) * 16 * g.K);
+        const int np = g.K > 1 ? g.K - 1 : 1;
+        g.ptA = (uint64_t *)take(sizeof(uint64_t) * (size_t)np * a_cap(g));
+        g.ptA_off = (int32_t *)take(sizeof(int32_t) * np);
+        g.ptA_len = (int32_t *)take(sizeof(int32_t) * np);
+        g.ptB = (uint64_t *)take(sizeof(uint64_t) * 64 * np);
+        g.U = (int32_t *)take(sizeof(int32_t) * 64 * (size_t)g.nslots);
+        g.swapmask = (uint32_t *)take(sizeof(uint32_t) * 2 * (size_t)g.W * g.R * np);
+        g.acc = (unsigned long long *)take(sizeof(unsigned long long) * (size_t)g.W * 64 * np);
+        const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
+        g.Cacc = (long long *)take(sizeof(long long) * nc);
+        g.Qacc = (long long *)take(sizeof(long long) * nc);
+        g.Pacc = (long long *)take(sizeof(long long) * (size_t)g.W * 64 * g.K);
+        g.outC = (double *)take(sizeof(double) * nc);
+        g.outQ = (double *)take(sizeof(double) * nc);
+        g.outP = (double *)take(sizeof(double) * (size_t)g.W * 64 * g.K);
+        // one (w, j) pair at least, up to the cap
+        const size_t per = measure_scratch_words_per_pair(g);
+        size_t want = kScratchCap / sizeof(uint64_t);
+        if (want < per) want = per;
+        const size_t all = per * (size_t)g.W * g.K;
+        if (want > all) want = all;
+        if (want > sw) sw = want;
+    }
+    *scratch = (uint64_t *)take(sizeof(uint64_t) * sw);
+    *scratch_words = sw;
+    return off;
+}
+
+// ---- acceptance tables (host FP64, integer results) ----------------------
+uint32_t met_threshold(double k, int Sh) {
+    const double p = std::exp(-(2.0 * k * (double)Sh));
+    return (uint32_t)std::floor(p * 4294967296.0);
+}
+
+uint32_t hb_threshold(double k, int h) {
+    const double p = 1.0 / (1.0 + std::exp(-(2.0 * k * (double)h)));
+    double t = std::floor(p * 4294967296.0);
+    if (t > 4294967295.0) t = 4294967295.0;
+    return (uint32_t)t;
+}
+
+uint64_t pt_factor(double delta, long long n) {
+    return (uint64_t)std::floor(std::exp(-(delta * (double)n)) * 4294967296.0);
+}
+
+}  // namespace
+
+struct qsg_ctx {
+    std::vector<qsg_shape> shapes;
+    std::vector<Group> groups;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    int *d_err = nullptr;
+    uint64_t *scratch = nullptr;
+    size_t scratch_words = 0;
+    cudaStream_t stream = nullptr;
+    uint64_t seed = 0;
+    bool initialised = false;
+    bool energy_fresh = false;
+    uint32_t sweeps = 0, swaps = 0;
+    long long n_meas = 0;
+    std::string last_cuda;
+};
+
+static qsg_status cuda_fail(qsg_ctx *c, cudaError_t e) {
+    if (e == cudaSuccess) return QSG_OK;
+    c->last_cuda = cudaGetErrorString(e);
+    return QSG_ERR_CUDA;
+}
+
+#define QSG_CUDA(c, expr)                                  \
+    do {                                                   \
+        cudaError_t _e = (expr);                           \
+        if (_e != cudaSuccess) return cuda_fail((c), _e);  \
+    } while (0)
+
+static qsg_status check_device_flag(qsg_ctx *c) {
+    int h = 0;
+    QSG_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    QSG_CUDA(c, cudaStreamSynchronize(c->stream));
+    return h == DEVERR_NONE ? QSG_OK : QSG_ERR_TIMEOUT;
+}
+
+extern "C" {
+
+size_t qsg_workspace_bytes(const qsg_shape *shapes, int32_t n_groups) {
+    if (!shapes || n_groups < 1 || n_groups > 255) return 0;
+    std::vector<Group> gs;
+    for (int i = 0; i < n_groups; ++i) {
+        if (!valid_shape(shapes[i])) return 0;
+        gs.push_back(describe(shapes[i], i));
+    }
+    int *e;
+    uint64_t *s;
+    size_t sw;
+    return carve(gs, nullptr, &e, &s, &sw);
+}
+
+qsg_status qsg_create(qsg_ctx **out, const qsg_shape *shapes, int32_t n_groups, void *d_workspace,
+                      size_t workspace_bytes, void *cuda_stream) {
+    if (!out || !shapes) return QSG_ERR_ARG;
+    *out = nullptr;
+    if (n_groups < 1 || n_groups > 255) return QSG_ERR_ARG;
+    for (int i = 0; i < n_groups; ++i)
+        if (!valid_shape(shapes[i])) return QSG_ERR_SHAPE;
+    const size_t need = qsg_workspace_bytes(shapes, n_groups);
+    if (!d_workspace || workspace_bytes < need || ((uintptr_t)d_workspace % kAlign) != 0) return QSG_ERR_WORKSPACE;
+    qsg_ctx *c = new qsg_ctx();
+    c->shapes.assign(shapes, shapes + n_groups);
+    for (int i = 0; i < n_groups; ++i) c->groups.push_back(describe(shapes[i], i));
+    c->ws = (char *)d_workspace;
+    c->ws_bytes = workspace_bytes;
+    carve(c->groups, c->ws, &c->d_err, &c->scratch, &c->scratch_words);
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return QSG_ERR_CUDA;
+    }
+    *out = c;
+    return QSG_OK;
+}
+
+void qsg_destroy(qsg_ctx *ctx) { delete ctx; }
+
+qsg_status qsg_set_stream(qsg_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return QSG_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return QSG_OK;
+}
+
+qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders) {
+    if (!ctx || !k_ladders) return QSG_ERR_ARG;
+    // validate every ladder and build every table before touching the device
+    std::vector<std::vector<uint32_t>> thr(ctx->groups.size());
+    std::vector<std::vector<uint64_t>> A(ctx->groups.size()), B(ctx->groups.size());
+    std::vector<std::vector<int32_t>> Aoff(ctx->groups.size()), Alen(ctx->groups.size());
+    const double *lad = k_ladders;
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+        const Group &g = ctx->groups[gi];
+        for (int j = 0; j < g.K; ++j) {
+            if (!(lad[j] > 0.0) || !(lad[j] < 3.0)) return QSG_ERR_ARG;
+            if (j > 0 && !(lad[j] > lad[j - 1])) return QSG_ERR_ARG;
+        }
+        thr[gi].assign(16 * (size_t)g.K, 0u);
+        for (int j = 0; j < g.K; ++j) {
+            for (int c = 0; c < 3; ++c) thr[gi][16 * j + c] = met_threshold(lad[j], 2 * (c + 1));
+            for (int n = 0; n < 7; ++n) thr[gi][16 * j + 8 + n] = hb_threshold(lad[j], 6 - 2 * n);
+            // the bitsliced comparison in the sweep kernels relies on monotone tables
+            for (int c = 0; c < 2; ++c)
+                if (thr[gi][16 * j + c] < thr[gi][16 * j + c + 1]) return QSG_ERR_ARG;
+            for (int n = 0; n < 6; ++n)
+                if (thr[gi][16 * j + 8 + n] < thr[gi][16 * j + 9 + n]) return QSG_ERR_ARG;
+        }
+        const int np = g.K > 1 ? g.K - 1 : 1;
+        const long long nmax_blocks = (6LL * g.N >> 6) + 1;
+        B[gi].assign(64 * (size_t)np, 0);
+        Aoff[gi].assign(np, 0);
+        Alen[gi].assign(np, 0);
+        for (int i = 0; i + 1 < g.K; ++i) {
+            const double delta = lad[i + 1] - lad[i];
+            for (int r = 0; r < 64; ++r) B[gi][64 * i + r] = pt_factor(delta, r);
+            long long len = 0;
+            while (len < nmax_blocks && pt_factor(delta, 64 * len) != 0) ++len;
+            if (len > kMaxA) return QSG_ERR_ARG;  // ladder spacing too fine for the table
+            Aoff[gi][i] = (int32_t)(i * a_cap(g));
+            Alen[gi][i] = (int32_t)len;
+            A[gi].resize((size_t)(i + 1) * a_cap(g), 0);
+            for (long long m = 0; m < len; ++m) A[gi][(size_t)i * a_cap(g) + m] = pt_factor(delta, 64 * m);
+        }
+        lad += g.K;
+    }
+    ctx->seed = seed;
+    cudaStream_t st = ctx->stream;
+    for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
+        const Group &g = ctx->groups[gi];
+        const int np = g.K > 1 ? g.K - 1 : 1;
+        QSG_CUDA(ctx, cudaMemcpyAsync(g.thr, thr[gi].data(), sizeof(uint32_t) * thr[gi].size(), cudaMemcpyHostToDevice, st));
+        if (!A[gi].empty())
+            QSG_CUDA(ctx, cudaMemcpyAsync(g.ptA, A[gi].data(), sizeof(uint64_t) * A[gi].size(), cudaMemcpyHostToDevice, st));
+        QSG_CUDA(ctx, cudaMemcpyAsync(g.ptB, B[gi].data(), sizeof(uint64_t) * B[gi].size(), cudaMemcpyHostToDevice, st));
+        QSG_CUDA(ctx, cudaMemcpyAsync(g.ptA_off, Aoff[gi].data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, st));
+        QSG_CUDA(ctx, cudaMemcpyAsync(g.ptA_len, Alen[gi].data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice, st));
+        QSG_CUDA(ctx, launch_init_couplings(g, seed, st));
+        QSG_CUDA(ctx, launch_init_spins(g, seed, st));
+        const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
+        QSG_CUDA(ctx, cudaMemsetAsync(g.Cacc, 0, sizeof(long long) * nc, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.Qacc, 0, sizeof(long long) * nc, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.Pacc, 0, sizeof(long long) * (size_t)g.W * 64 * g.K, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.acc, 0, sizeof(unsigned long long) * (size_t)g.W * 64 * np, st));
+    }
+    // host copies of the tables must stay alive until the copies complete
+    QSG_CUDA(ctx, cudaStreamSynchronize(st));
+    ctx->sweeps = 0;
+    ctx->swaps = 0;
+    ctx->n_meas = 0;
+    ctx->energy_fresh = false;
+    ctx->initialised = true;
+    return QSG_OK;
+}
+
+qsg_status qsg_set_couplings(qsg_ctx *ctx, int32_t group, const int8_t *J_host) {
+    if (!ctx || !J_host || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    const int L2 = g.L * g.L;
+    std::vector<uint64_t> jx((size_t)g.W * L2, 0), jy((size_t)g.W * L2, 0);
+    for (int b = 0; b < g.n_samples; ++b)
+        for (int d = 0; d < 2; ++d)
+            for (int n = 0; n < L2; ++n) {
+                const int8_t v = J_host[((size_t)b * 2 + d) * L2 + n];
+                if (v != 1 && v != -1) return QSG_ERR_ARG;
+                if (v == -1) (d == 0 ? jx : jy)[(size_t)(b / 64) * L2 + n] |= 1ull << (b % 64);
+            }
+    QSG_CUDA(ctx, cudaMemcpyAsync(g.Jx, jx.data(), sizeof(uint64_t) * jx.size(), cudaMemcpyHostToDevice, ctx->stream));
+    QSG_CUDA(ctx, cudaMemcpyAsync(g.Jy, jy.data(), sizeof(uint64_t) * jy.size(), cudaMemcpyHostToDevice, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->energy_fresh = false;
+    return QSG_OK;
+}
+
+qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
+    if (!ctx || n_sweeps < 0) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
+    for (int it = 0; it < n_sweeps; ++it) {
+        for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_sweep_reference(g, ctx->sweeps, ctx->seed, ctx->stream));
+        ctx->sweeps++;
+    }
+    if (n_sweeps > 0) ctx->energy_fresh = false;
+    return QSG_OK;
+}
+
+static qsg_status ensure_energy(qsg_ctx *ctx) {
+    if (ctx->energy_fresh) return QSG_OK;
+    for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_energy(g, ctx->stream));
+    ctx->energy_fresh = true;
+    return QSG_OK;
+}
+
+qsg_status qsg_tempering_swap(qsg_ctx *ctx) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    qsg_status s = ensure_energy(ctx);
+    if (s != QSG_OK) return s;
+    for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_tempering(g, ctx->swaps, ctx->seed, ctx->stream));
+    ctx->swaps++;
+    return QSG_OK;
+}
+
+qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->stream));
+    ctx->n_meas++;
+    return QSG_OK;
+}
+
+qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw) {
+    if (!ctx || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
+    const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
+    const size_t np = (size_t)g.W * 64 * g.K;
+    std::vector<double> hc(nc), hq(nc), hp(np);
+    std::vector<long long> rc, rq, rp;
+    QSG_CUDA(ctx, cudaMemcpyAsync(hc.data(), g.outC, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaMemcpyAsync(hq.data(), g.outQ, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaMemcpyAsync(hp.data(), g.outP, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    if (raw) {
+        rc.resize(nc);
+        rq.resize(nc);
+        rp.resize(np);
+        QSG_CUDA(ctx, cudaMemcpyAsync(rc.data(), g.Cacc, sizeof(long long) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(rq.data(), g.Qacc, sizeof(long long) * nc, cudaMemcpyDeviceToHost, ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(rp.data(), g.Pacc, sizeof(long long) * np, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    qsg_status s = check_device_flag(ctx);
+    if (s != QSG_OK) return s;
+    const int S = g.n_samples, Sp = g.W * 64, K = g.K, nl = g.nlag;
+    const size_t outc = (size_t)g.R * S * K * nl;
+    for (int r = 0; r < g.R; ++r)
+        for (int b = 0; b < S; ++b) {
+            const size_t src = (((size_t)r * Sp + b) * K) * nl, dst = (((size_t)r * S + b) * K) * nl;
+            if (C) std::memcpy(C + dst, hc.data() + src, sizeof(double) * K * nl);
+            if (Q2) std::memcpy(Q2 + dst, hq.data() + src, sizeof(double) * K * nl);
+            if (raw) {
+                std::memcpy(raw + dst, rc.data() + src, sizeof(long long) * K * nl);
+                std::memcpy(raw + outc + dst, rq.data() + src, sizeof(long long) * K * nl);
+            }
+        }
+    for (int b = 0; b < S; ++b) {
+        if (q2) std::memcpy(q2 + (size_t)b * K, hp.data() + (size_t)b * K, sizeof(double) * K);
+        if (raw) std::memcpy(raw + 2 * outc + (size_t)b * K, rp.data() + (size_t)b * K, sizeof(long long) * K);
+    }
+    return QSG_OK;
+}
+
+qsg_status qsg_read_energies(qsg_ctx *ctx, int32_t group, int64_t *E_host) {
+    if (!ctx || !E_host || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    qsg_status s = ensure_energy(ctx);
+    if (s != QSG_OK) return s;
+    const Group &g = ctx->groups[group];
+    std::vector<int32_t> U((size_t)g.nslots * 64);
+    QSG_CUDA(ctx, cudaMemcpyAsync(U.data(), g.U, sizeof(int32_t) * U.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < g.n_samples; ++b)
+        for (int r = 0; r < g.R; ++r)
+            for (int j = 0; j < g.K; ++j) {
+                const size_t slot = ((size_t)(b / 64) * g.R + r) * g.K + j;
+                E_host[((size_t)b * g.R + r) * g.K + j] = 2LL * U[slot * 64 + (b % 64)] - 3LL * g.N;
+            }
+    return QSG_OK;
+}
+
+qsg_status qsg_read_accepts(qsg_ctx *ctx, int32_t group, int64_t *acc_host) {
+    if (!ctx || !acc_host || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    const int np = g.K > 1 ? g.K - 1 : 1;
+    std::vector<unsigned long long> a((size_t)g.W * 64 * np);
+    QSG_CUDA(ctx, cudaMemcpyAsync(a.data(), g.acc, sizeof(unsigned long long) * a.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t i = 0; i < (size_t)g.n_samples * np; ++i) acc_host[i] = (int64_t)a[i];
+    return QSG_OK;
+}
+
+qsg_status qsg_get_spins(qsg_ctx *ctx, int32_t group, uint64_t *host) {
+    if (!ctx || !host || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, cudaMemcpyAsync(host, g.S, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QSG_OK;
+}
+
+qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host) {
+    if (!ctx || !host || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, cudaMemcpyAsync(g.S, host, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyHostToDevice, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->energy_fresh = false;
+    return QSG_OK;
+}
+
+qsg_status qsg_get_counters(qsg_ctx *ctx, uint32_t *sweeps, uint32_t *swaps, int64_t *n_meas) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (sweeps) *sweeps = ctx->sweeps;
+    if (swaps) *swaps = ctx->swaps;
+    if (n_meas) *n_meas = ctx->n_meas;
+    return QSG_OK;
+}
+
+qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64_t n_meas) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    ctx->sweeps = sweeps;
+    ctx->swaps = swaps;
+    if (n_meas >= 0) ctx->n_meas = n_meas;
+    return QSG_OK;
+}
+
+uint64_t qsg_kernel_launches(void) { return (uint64_t)g_launches.load(); }
+
+const char *qsg_strerror(qsg_status status) {
+    switch (status) {
+        case QSG_OK: return "ok";
+        case QSG_ERR_ARG: return "invalid argument";
+        case QSG_ERR_SHAPE: return "invalid group shape";
+        case QSG_ERR_CUDA: return "CUDA runtime error";
+        case QSG_ERR_TIMEOUT: return "bounded device wait gave up";
+        case QSG_ERR_STATE: return "call out of order";
+        case QSG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    }
+    return "unknown status";
+}
+
+const char *qsg_last_cuda_error(qsg_ctx *ctx) { return ctx ? ctx->last_cuda.c_str() : ""; }
+
+}  // extern "C"

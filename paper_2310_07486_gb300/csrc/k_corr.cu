@@ -1,0 +1,179 @@
+// k_corr.cu -- imaginary-time correlators C(tau), Q2(tau) and the equal-time
+// replica overlap (Eqs. (C_A_transfer), (def-C-Q2-tau)), accumulated exactly
+// in int64, and their FP64 finish.
+//
+// The multispin words hold 64 samples per site.  The correlators need, per
+// sample, the overlap of two tau slices summed over sites, so the slices are
+// first transposed into x-packed words (64 sites per word, one sample per
+// row) in a scratch buffer; an overlap is then L^2 - 2 popc(a ^ b).
+#include "qsg_launch.h"
+
+namespace qsg {
+
+size_t measure_scratch_words_per_pair(const Group &g) {
+    return (size_t)g.R * 64 * g.Ltau * g.nwx;
+}
+
+// scratch layout for a batch of (w, j) pairs: [pair][r][b][tau][nwx]
+__global__ void k_transpose(Group g, int p0, int npairs, uint64_t *P) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long total = (long long)npairs * g.R * g.Ltau * g.nwx;
+    if (warp >= total) return;
+    const int L2 = g.L * g.L;
+    const int gx = (int)(warp % g.nwx);
+    const int t = (int)((warp / g.nwx) % g.Ltau);
+    const int sb = (int)(warp / ((long long)g.nwx * g.Ltau));
+    const int pb = sb / g.R, r = sb % g.R;
+    const int p = p0 + pb, w = p / g.K, j = p % g.K;
+    const size_t s = ((size_t)w * g.R + r) * g.K + j;
+    const uint64_t *src = g.S + s * g.N + (size_t)t * L2;
+    const int s0 = gx * 64 + lane, s1 = s0 + 32;
+    const uint64_t w0 = s0 < L2 ? src[s0] : 0ull;
+    const uint64_t w1 = s1 < L2 ? src[s1] : 0ull;
+    uint64_t keep0 = 0, keep1 = 0;
+#pragma unroll 8
+    for (int b = 0; b < 64; ++b) {
+        const uint32_t lo = __ballot_sync(0xffffffffu, (w0 >> b) & 1ull);
+        const uint32_t hi = __ballot_sync(0xffffffffu, (w1 >> b) & 1ull);
+        const uint64_t word = (uint64_t)lo | ((uint64_t)hi << 32);
+        if (lane == (b & 31)) {
+            if (b < 32) keep0 = word; else keep1 = word;
+        }
+    }
+    uint64_t *dst = P + (size_t)sb * 64 * g.Ltau * g.nwx;
+    dst[((size_t)lane * g.Ltau + t) * g.nwx + gx] = keep0;
+    dst[((size_t)(lane + 32) * g.Ltau + t) * g.nwx + gx] = keep1;
+}
+
+// One block per (slot of the batch, sample bit): all lags of one sample.
+__global__ void __launch_bounds__(256) k_gram(Group g, int p0, const uint64_t *P, int use_smem) {
+    extern __shared__ uint64_t sh[];
+    const int sb = blockIdx.x / 64, b = blockIdx.x % 64;
+    const int pb = sb / g.R, r = sb % g.R;
+    const int p = p0 + pb, w = p / g.K, j = p % g.K;
+    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L;
+    const uint64_t *src = P + ((size_t)sb * 64 + b) * Lt * nwx;
+    if (use_smem) {
+        for (int i = threadIdx.x; i < Lt * nwx; i += blockDim.x) sh[i] = src[i];
+        __syncthreads();
+        src = sh;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int lag = warp; lag < g.nlag; lag += nwarp) {
+        long long cs = 0, qs = 0;
+        for (int t1 = lane; t1 < Lt; t1 += 32) {
+            int t2 = t1 + lag;
+            int sgn = 1;
+            if (t2 >= Lt) {
+                t2 -= Lt;
+                if (g.boundary == 1) sgn = -1;
+            }
+            int d = 0;
+            for (int x = 0; x < nwx; ++x) d += __popcll(src[t1 * nwx + x] ^ src[t2 * nwx + x]);
+            const long long c = (long long)(L2 - 2 * d);
+            cs += sgn * c;
+            qs += c * c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cs += __shfl_down_sync(0xffffffffu, cs, o);
+            qs += __shfl_down_sync(0xffffffffu, qs, o);
+        }
+        if (lane == 0) {
+            const size_t idx = ((((size_t)r * g.W * 64) + (size_t)w * 64 + b) * g.K + j) * g.nlag + lag;
+            g.Cacc[idx] += cs;
+            g.Qacc[idx] += qs;
+        }
+    }
+}
+
+// Equal-time overlap of every replica pair at one ladder position.
+__global__ void __launch_bounds__(256) k_overlap(Group g, int p0, const uint64_t *P) {
+    __shared__ long long red[256 / 32];
+    const int pb = blockIdx.x / 64, b = blockIdx.x % 64;
+    const int p = p0 + pb, w = p / g.K, j = p % g.K;
+    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L;
+    const size_t plane = (size_t)Lt * nwx;
+    long long sum = 0;
+    for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
+        for (int ra = 0; ra < g.R; ++ra) {
+            const uint64_t *A = P + (((size_t)pb * g.R + ra) * 64 + b) * plane + (size_t)t * nwx;
+            for (int rb = ra + 1; rb < g.R; ++rb) {
+                const uint64_t *B = P + (((size_t)pb * g.R + rb) * 64 + b) * plane + (size_t)t * nwx;
+                int d = 0;
+                for (int x = 0; x < nwx; ++x) d += __popcll(A[x] ^ B[x]);
+                const long long q = (long long)(L2 - 2 * d);
+                sum += q * q;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long tot = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
+        g.Pacc[((size_t)w * 64 + b) * g.K + j] += tot;
+    }
+}
+
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, cudaStream_t st) {
+    const size_t per_pair = measure_scratch_words_per_pair(g);
+    int batch = (int)(scratch_words / per_pair);
+    if (batch < 1) return cudaErrorInvalidValue;
+    const int npairs_total = g.W * g.K;
+    const size_t sh_bytes = (size_t)g.Ltau * g.nwx * sizeof(uint64_t);
+    const int use_smem = sh_bytes <= 200 * 1024 ? 1 : 0;
+    if (use_smem) {
+        cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    for (int p0 = 0; p0 < npairs_total; p0 += batch) {
+        const int np = min(batch, npairs_total - p0);
+        const long long warps = (long long)np * g.R * g.Ltau * g.nwx;
+        count_launches(1);
+        k_transpose<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, p0, np, scratch);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        count_launches(1);
+        k_gram<<<np * g.R * 64, 256, use_smem ? sh_bytes : 0, st>>>(g, p0, scratch, use_smem);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (g.R >= 2) {
+            count_launches(1);
+            k_overlap<<<np * 64, 256, 0, st>>>(g, p0, scratch);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+// C = C_acc / (n_meas L^2 L_tau), Q2 = Q_acc / (n_meas L^4 L_tau),
+// q2 = P_acc / (n_meas n_pairs L^4 L_tau); IEEE division, no fused operations.
+__global__ void k_finish(Group g, double nm) {
+    const double L2 = (double)(g.L * g.L), Lt = (double)g.Ltau;
+    const double pairs = (double)(g.R * (g.R - 1) / 2);
+    const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
+    const size_t np = (size_t)g.W * 64 * g.K;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nc; i += (size_t)gridDim.x * blockDim.x) {
+        g.outC[i] = __ddiv_rn((double)g.Cacc[i], __dmul_rn(__dmul_rn(nm, L2), Lt));
+        g.outQ[i] = __ddiv_rn((double)g.Qacc[i], __dmul_rn(__dmul_rn(__dmul_rn(nm, L2), L2), Lt));
+        if (i < np)
+            g.outP[i] = __ddiv_rn((double)g.Pacc[i],
+                                  __dmul_rn(__dmul_rn(__dmul_rn(__dmul_rn(nm, pairs), L2), L2), Lt));
+    }
+}
+
+cudaError_t launch_finish(const Group &g, long long n_meas, cudaStream_t st) {
+    const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
+    long long blocks = (long long)((nc + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    count_launches(1);
+    k_finish<<<(int)blocks, 256, 0, st>>>(g, (double)n_meas);
+    return cudaGetLastError();
+}
+
+}  // namespace qsg

@@ -1,0 +1,38 @@
+// qsg_launch.h -- host-side launchers of the sm_103a kernels (internal).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "qsg_device.cuh"
+
+namespace qsg {
+
+// Process-wide count of kernel launches (qsg_kernel_launches()).
+void count_launches(int n);
+
+// Device-side status word: non-zero after a bounded wait gave up.
+enum : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1 };
+
+cudaError_t launch_init_couplings(const Group &g, uint64_t seed, cudaStream_t st);
+cudaError_t launch_init_spins(const Group &g, uint64_t seed, cudaStream_t st);
+
+// One full sweep (colour 0 then colour 1) of every slot of the group.
+// The "reference" variant runs one launch per colour with one thread per site.
+cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed, cudaStream_t st);
+
+// Unsatisfied-bond counts U[slot][bit] of the current configurations.
+cudaError_t launch_energy(const Group &g, cudaStream_t st);
+
+// Tempering step `m`: decisions (and U bookkeeping), then the spin-bit moves.
+cudaError_t launch_tempering(const Group &g, uint32_t m, uint64_t seed, cudaStream_t st);
+
+// Correlator accumulation through the x-packed transposed scratch buffer.
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, cudaStream_t st);
+
+// FP64 finish into g.outC / g.outQ / g.outP.
+cudaError_t launch_finish(const Group &g, long long n_meas, cudaStream_t st);
+
+// Scratch words the correlator path needs for one (w, j) pair of the group.
+size_t measure_scratch_words_per_pair(const Group &g);
+
+}  // namespace qsg

@@ -1,0 +1,278 @@
+"""Python binding of the C ABI in ``include/qsg.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: all of it runs in the sm_103a kernels of
+``libqsg.so``.  PyTorch provides the device workspace and the CUDA stream.
+If the library cannot be loaded the binding raises; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libqsg.so")
+_lib = None
+
+METROPOLIS, HEATBATH = 0, 1
+PBC, APBC = 0, 1
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "invalid group shape", -3: "CUDA runtime error",
+          -4: "bounded device wait gave up", -5: "call out of order", -6: "workspace missing or too small"}
+
+
+class QSGError(RuntimeError):
+    def __init__(self, status, what, detail=""):
+        super().__init__("%s failed: %s%s" % (what, STATUS.get(status, status), (" (" + detail + ")") if detail else ""))
+        self.status = status
+
+
+class qsg_shape(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("Ltau", ctypes.c_int32), ("n_samples", ctypes.c_int32),
+                ("n_replicas", ctypes.c_int32), ("n_k", ctypes.c_int32), ("algo", ctypes.c_int32),
+                ("boundary", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def load_library(path: str | None = None):
+    """Load libqsg.so (building it first with nvcc if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _LIB_PATH
+    if not os.path.exists(path):
+        from . import build as _build
+        _build.build()
+    lib = ctypes.CDLL(path)
+    vp, i32, u32, u64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_size_t
+    lib.qsg_workspace_bytes.restype = sz
+    lib.qsg_workspace_bytes.argtypes = [vp, i32]
+    lib.qsg_create.restype = i32
+    lib.qsg_create.argtypes = [ctypes.POINTER(vp), vp, i32, vp, sz, vp]
+    lib.qsg_destroy.restype = None
+    lib.qsg_destroy.argtypes = [vp]
+    lib.qsg_set_stream.restype = i32
+    lib.qsg_set_stream.argtypes = [vp, vp]
+    lib.qsg_init_samples.restype = i32
+    lib.qsg_init_samples.argtypes = [vp, u64, vp]
+    lib.qsg_set_couplings.restype = i32
+    lib.qsg_set_couplings.argtypes = [vp, i32, vp]
+    lib.qsg_sweep.restype = i32
+    lib.qsg_sweep.argtypes = [vp, i32]
+    lib.qsg_tempering_swap.restype = i32
+    lib.qsg_tempering_swap.argtypes = [vp]
+    lib.qsg_measure_correlators.restype = i32
+    lib.qsg_measure_correlators.argtypes = [vp]
+    lib.qsg_read_correlators.restype = i32
+    lib.qsg_read_correlators.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.qsg_read_energies.restype = i32
+    lib.qsg_read_energies.argtypes = [vp, i32, vp]
+    lib.qsg_read_accepts.restype = i32
+    lib.qsg_read_accepts.argtypes = [vp, i32, vp]
+    lib.qsg_get_spins.restype = i32
+    lib.qsg_get_spins.argtypes = [vp, i32, vp]
+    lib.qsg_set_spins.restype = i32
+    lib.qsg_set_spins.argtypes = [vp, i32, vp]
+    lib.qsg_get_counters.restype = i32
+    lib.qsg_get_counters.argtypes = [vp, vp, vp, vp]
+    lib.qsg_set_counters.restype = i32
+    lib.qsg_set_counters.argtypes = [vp, u32, u32, ctypes.c_int64]
+    lib.qsg_kernel_launches.restype = ctypes.c_uint64
+    lib.qsg_kernel_launches.argtypes = []
+    lib.qsg_strerror.restype = ctypes.c_char_p
+    lib.qsg_strerror.argtypes = [i32]
+    lib.qsg_last_cuda_error.restype = ctypes.c_char_p
+    lib.qsg_last_cuda_error.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return ["qsg_workspace_bytes", "qsg_create", "qsg_destroy", "qsg_set_stream", "qsg_init_samples",
+            "qsg_set_couplings", "qsg_sweep", "qsg_tempering_swap", "qsg_measure_correlators",
+            "qsg_read_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
+            "qsg_get_counters", "qsg_set_counters", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
+
+
+def qsg_kernel_launches() -> int:
+    return int(load_library().qsg_kernel_launches())
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+@dataclass
+class Shape:
+    L: int
+    Ltau: int
+    n_samples: int
+    n_replicas: int
+    n_k: int
+    algo: int = METROPOLIS
+    boundary: int = PBC
+
+    def c(self):
+        return qsg_shape(self.L, self.Ltau, self.n_samples, self.n_replicas, self.n_k, self.algo, self.boundary, 0)
+
+    @property
+    def words(self):
+        return (self.n_samples + 63) // 64
+
+    @property
+    def slots(self):
+        return self.words * self.n_replicas * self.n_k
+
+    @property
+    def n_lag(self):
+        return self.Ltau // 2 + 1
+
+
+def _shape_array(shapes):
+    arr = (qsg_shape * len(shapes))()
+    for i, s in enumerate(shapes):
+        arr[i] = s.c()
+    return arr
+
+
+def qsg_workspace_bytes(shapes) -> int:
+    arr = _shape_array(shapes)
+    return int(load_library().qsg_workspace_bytes(ctypes.cast(arr, ctypes.c_void_p), len(shapes)))
+
+
+class Context:
+    """A qsg_ctx over a torch-allocated device workspace.
+
+    Methods map one-to-one onto the C entry points of the same name.
+    """
+
+    def __init__(self, shapes, device=None, stream=None):
+        import torch
+        self.lib = load_library()
+        self.shapes = list(shapes)
+        self._arr = _shape_array(self.shapes)
+        nbytes = qsg_workspace_bytes(self.shapes)
+        if nbytes == 0:
+            raise QSGError(-2, "qsg_workspace_bytes")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        # torch's caching allocator returns blocks aligned to at least 512 bytes
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = self._check(self.lib.qsg_create(ctypes.byref(h), ctypes.cast(self._arr, ctypes.c_void_p), len(self.shapes),
+                                             ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                             ctypes.c_void_p(self.stream.cuda_stream)), "qsg_create", ctx=False)
+        self.h = h
+
+    def _check(self, status, what, ctx=True):
+        if status != 0:
+            detail = ""
+            if ctx and status == -3:
+                detail = self.lib.qsg_last_cuda_error(self.h).decode()
+            raise QSGError(status, what, detail)
+        return status
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qsg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- calls ----------------------------------------------------------
+    def qsg_set_stream(self, stream):
+        self.stream = stream
+        self._check(self.lib.qsg_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)), "qsg_set_stream")
+
+    def qsg_init_samples(self, seed, ladders):
+        lad = np.ascontiguousarray(np.concatenate([np.asarray(l, dtype=np.float64).ravel() for l in ladders]))
+        self._check(self.lib.qsg_init_samples(self.h, int(seed) & ((1 << 64) - 1), _ptr(lad)), "qsg_init_samples")
+
+    def qsg_set_couplings(self, group, J):
+        J = np.ascontiguousarray(J, dtype=np.int8)
+        self._check(self.lib.qsg_set_couplings(self.h, group, _ptr(J)), "qsg_set_couplings")
+
+    def qsg_sweep(self, n=1):
+        self._check(self.lib.qsg_sweep(self.h, int(n)), "qsg_sweep")
+
+    def qsg_tempering_swap(self):
+        self._check(self.lib.qsg_tempering_swap(self.h), "qsg_tempering_swap")
+
+    def qsg_measure_correlators(self):
+        self._check(self.lib.qsg_measure_correlators(self.h), "qsg_measure_correlators")
+
+    def qsg_read_correlators(self, group=0, raw=False):
+        s = self.shapes[group]
+        shp = (s.n_replicas, s.n_samples, s.n_k, s.n_lag)
+        C = np.zeros(shp)
+        Q = np.zeros(shp)
+        P = np.zeros((s.n_samples, s.n_k))
+        nc = int(np.prod(shp))
+        R = np.zeros(2 * nc + s.n_samples * s.n_k, dtype=np.int64) if raw else None
+        self._check(self.lib.qsg_read_correlators(self.h, group, _ptr(C), _ptr(Q), _ptr(P),
+                                                  None if R is None else _ptr(R)), "qsg_read_correlators")
+        out = dict(C=C, Q2=Q, q2=P)
+        if raw:
+            out.update(C_raw=R[:nc].reshape(shp), Q2_raw=R[nc:2 * nc].reshape(shp),
+                       q2_raw=R[2 * nc:].reshape(s.n_samples, s.n_k))
+        return out
+
+    def qsg_read_energies(self, group=0):
+        s = self.shapes[group]
+        E = np.zeros((s.n_samples, s.n_replicas, s.n_k), dtype=np.int64)
+        self._check(self.lib.qsg_read_energies(self.h, group, _ptr(E)), "qsg_read_energies")
+        return E
+
+    def qsg_read_accepts(self, group=0):
+        s = self.shapes[group]
+        A = np.zeros((s.n_samples, max(s.n_k - 1, 1)), dtype=np.int64)
+        self._check(self.lib.qsg_read_accepts(self.h, group, _ptr(A)), "qsg_read_accepts")
+        return A
+
+    def qsg_get_spins(self, group=0):
+        s = self.shapes[group]
+        out = np.zeros((s.slots, s.Ltau, s.L, s.L), dtype=np.uint64)
+        self._check(self.lib.qsg_get_spins(self.h, group, _ptr(out)), "qsg_get_spins")
+        return out
+
+    def qsg_set_spins(self, group, words):
+        words = np.ascontiguousarray(words, dtype=np.uint64)
+        self._check(self.lib.qsg_set_spins(self.h, group, _ptr(words)), "qsg_set_spins")
+
+    def qsg_get_counters(self):
+        a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()
+        self._check(self.lib.qsg_get_counters(self.h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+                    "qsg_get_counters")
+        return a.value, b.value, c.value
+
+
+    def qsg_set_counters(self, sweeps, swaps, n_meas=-1):
+        self._check(self.lib.qsg_set_counters(self.h, int(sweeps), int(swaps), int(n_meas)), "qsg_set_counters")
+
+
+# ---- host-side layout helpers (no method arithmetic) -----------------------
+def unpack_spins(words: np.ndarray, shape: Shape) -> np.ndarray:
+    """uint64 words [slots][Ltau][L][L] -> int8 spins [n_samples][R][K][Ltau][L][L]."""
+    W, R, K = shape.words, shape.n_replicas, shape.n_k
+    w = words.reshape(W, R, K, shape.Ltau, shape.L, shape.L)
+    out = np.empty((shape.n_samples, R, K, shape.Ltau, shape.L, shape.L), dtype=np.int8)
+    for b in range(shape.n_samples):
+        bits = (w[b // 64] >> np.uint64(b % 64)) & np.uint64(1)
+        out[b] = (1 - 2 * bits.astype(np.int8))
+    return out
+
+
+def pack_spins(spins: np.ndarray, shape: Shape) -> np.ndarray:
+    """int8 spins [n_samples][R][K][Ltau][L][L] -> uint64 words (padding bits 0)."""
+    W = shape.words
+    words = np.zeros((W, shape.n_replicas, shape.n_k, shape.Ltau, shape.L, shape.L), dtype=np.uint64)
+    for b in range(shape.n_samples):
+        bit = (spins[b] < 0).astype(np.uint64) << np.uint64(b % 64)
+        words[b // 64] |= bit
+    return words.reshape(shape.slots, shape.Ltau, shape.L, shape.L)

@@ -1,0 +1,66 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports
+every entry point that include/qsg.h declares, and validates shapes."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_07486_gb300 import qsg as Q
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_entry_points():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names.update(re.findall(r"\b(qsg_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = Q.load_library()
+    names = declared_entry_points()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(Q.exported_symbols()) <= set(names)
+
+
+@pytest.mark.parametrize("bad", [
+    Q.Shape(7, 8, 1, 1, 1), Q.Shape(0, 8, 1, 1, 1), Q.Shape(8, 7, 1, 1, 1), Q.Shape(8, 8, 0, 1, 1),
+    Q.Shape(8, 8, 1, 0, 1), Q.Shape(8, 8, 1, 1, 0), Q.Shape(8, 8, 1, 1, 129), Q.Shape(34, 8, 1, 1, 1),
+    Q.Shape(8, 8, 1, 1, 1, algo=2), Q.Shape(8, 8, 1, 1, 1, boundary=3)])
+def test_invalid_shapes_are_rejected(bad):
+    assert Q.qsg_workspace_bytes([bad]) == 0
+
+
+def test_workspace_grows_with_the_state():
+    small = Q.qsg_workspace_bytes([Q.Shape(8, 16, 64, 2, 2)])
+    big = Q.qsg_workspace_bytes([Q.Shape(8, 32, 64, 2, 2)])
+    assert small > 0 and big > small
+    state = 24 * 24 * 2048 * 2 * 4 * 32 * 8
+    assert Q.qsg_workspace_bytes([Q.Shape(24, 2048, 128, 4, 32, Q.HEATBATH)]) > state
+
+
+def test_create_rejects_missing_workspace():
+    lib = Q.load_library()
+    arr = Q._shape_array([Q.Shape(8, 8, 1, 1, 1)])
+    h = ctypes.c_void_p()
+    st = lib.qsg_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), 1, None, 0, None)
+    assert st == -6 and not h.value
+    st = lib.qsg_create(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), 0, None, 0, None)
+    assert st == -1
+
+
+def test_calls_on_null_context_fail_cleanly():
+    lib = Q.load_library()
+    assert lib.qsg_sweep(None, 1) == -1
+    assert lib.qsg_tempering_swap(None) == -1
+    assert lib.qsg_measure_correlators(None) == -1
+    assert lib.qsg_strerror(-4) == b"bounded device wait gave up"

@@ -1,0 +1,212 @@
+"""GPU path (through the C ABI) against the CPU oracle, bit for bit.
+
+Spins, integer actions, tempering decisions and int64 correlator sums must be
+identical; the FP64 correlators must agree to 1e-12 relative (they are one
+IEEE division of identical integers, so in practice they are identical).
+Small cases cover several tiles, ragged sample counts (not a multiple of 64)
+and both boundary conditions; the full-size cases run in the bench's launch
+configuration and compare one sample, chosen at random, that the oracle
+simulates alone.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_2310_07486_gb300 import qsg as Q  # noqa: E402
+from paper_2310_07486_gb300 import workloads  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+def _pair(shape, ladder, seed, first=0, n_oracle=None, gid=0):
+    ctx = Q.Context([shape])
+    ctx.qsg_init_samples(seed, [ladder])
+    orc = oracle.OracleGroup(shape.L, shape.Ltau, n_oracle or shape.n_samples, shape.n_replicas, shape.n_k,
+                             algo=shape.algo, boundary=shape.boundary, group_id=gid, first_sample=first)
+    orc.init(seed, ladder)
+    return ctx, orc
+
+
+def _gpu_spins(ctx, shape, group=0, first=0, n=None):
+    words = ctx.qsg_get_spins(group)
+    S = Q.unpack_spins(words, shape)
+    n = n or shape.n_samples
+    return S[first:first + n]
+
+
+def _check_corr(gpu, orc_res):
+    for key in ("C_raw", "Q2_raw", "q2_raw"):
+        assert np.array_equal(gpu[key], orc_res[key]), key
+    for key in ("C", "Q2", "q2"):
+        a, b = gpu[key], orc_res[key]
+        both_nan = np.isnan(a) & np.isnan(b)
+        assert np.all(both_nan | (np.abs(a - b) <= RTOL * np.maximum(np.abs(b), 1e-300))), key
+
+
+@pytest.mark.parametrize("algo", [Q.METROPOLIS, Q.HEATBATH])
+@pytest.mark.parametrize("boundary", [Q.PBC, Q.APBC])
+def test_init_and_sweeps_match_oracle(algo, boundary):
+    shape = Q.Shape(8, 12, 70, 2, 2, algo, boundary)  # 2 words, ragged last word
+    lad = np.array([0.25, 0.31])
+    ctx, orc = _pair(shape, lad, seed=11)
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    for n in (1, 4):
+        ctx.qsg_sweep(n)
+        orc.sweep(n)
+        assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+
+
+@pytest.mark.parametrize("L,Ltau", [(2, 2), (2, 6), (6, 4), (32, 4)])
+def test_edge_shapes_match_oracle(L, Ltau):
+    shape = Q.Shape(L, Ltau, 65, 1, 2, Q.METROPOLIS, Q.APBC)
+    ctx, orc = _pair(shape, np.array([0.2, 0.4]), seed=5)
+    for _ in range(3):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        ctx.qsg_measure_correlators()
+        orc.measure()
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    _check_corr(ctx.qsg_read_correlators(raw=True), orc.read())
+
+
+@pytest.mark.parametrize("algo", [Q.METROPOLIS, Q.HEATBATH])
+def test_tempering_matches_oracle(algo):
+    shape = Q.Shape(6, 8, 70, 2, 5, algo, Q.PBC)
+    lad = workloads.uniform_ladder(0.15, 0.45, 5)
+    ctx, orc = _pair(shape, lad, seed=21)
+    for _ in range(8):
+        ctx.qsg_sweep(3)
+        orc.sweep(3)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    assert np.array_equal(ctx.qsg_read_accepts(), orc.accepts())
+    assert ctx.qsg_read_accepts().sum() > 0
+
+
+@pytest.mark.parametrize("boundary", [Q.PBC, Q.APBC])
+def test_correlators_match_oracle(boundary):
+    shape = Q.Shape(10, 40, 66, 3, 2, Q.HEATBATH, boundary)  # L^2 = 100: two x-packed words, ragged
+    lad = np.array([0.28, 0.33])
+    ctx, orc = _pair(shape, lad, seed=8)
+    for _ in range(4):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_measure_correlators()
+        orc.measure()
+    gpu = ctx.qsg_read_correlators(raw=True)
+    _check_corr(gpu, orc.read())
+    assert np.all(gpu["C"][..., 0] == 1.0) and np.all(gpu["Q2"][..., 0] == 1.0)
+
+
+def test_two_groups_of_different_size():
+    shapes = [Q.Shape(6, 8, 3, 2, 3, Q.METROPOLIS, Q.PBC), Q.Shape(8, 16, 66, 2, 2, Q.HEATBATH, Q.APBC)]
+    lads = [np.array([0.2, 0.3, 0.4]), np.array([0.25, 0.35])]
+    ctx = Q.Context(shapes)
+    ctx.qsg_init_samples(17, lads)
+    orcs = []
+    for gid, (s, l) in enumerate(zip(shapes, lads)):
+        o = oracle.OracleGroup(s.L, s.Ltau, s.n_samples, s.n_replicas, s.n_k, algo=s.algo, boundary=s.boundary,
+                               group_id=gid)
+        o.init(17, l)
+        orcs.append(o)
+    for _ in range(3):
+        ctx.qsg_sweep(2)
+        ctx.qsg_tempering_swap()
+        ctx.qsg_measure_correlators()
+        for o in orcs:
+            o.sweep(2)
+            o.swap()
+            o.measure()
+    for gid, (s, o) in enumerate(zip(shapes, orcs)):
+        assert np.array_equal(_gpu_spins(ctx, s, group=gid), o.spins())
+        _check_corr(ctx.qsg_read_correlators(gid, raw=True), o.read())
+        assert np.array_equal(ctx.qsg_read_accepts(gid), o.accepts())
+
+
+def test_smallest_workload_full_run():
+    """One sample, L=6, L_tau=32, k=0.29, 2 replicas, Metropolis, 2000 sweeps,
+    correlators every 10 sweeps: everything bit-exact."""
+    w = workloads.smallest()
+    shape, lad = w.shapes[0], w.ladders[0]
+    ctx, orc = _pair(shape, lad, seed=w.seed)
+    for _ in range(w.total_sweeps // w.measure_every):
+        ctx.qsg_sweep(w.measure_every)
+        orc.sweep(w.measure_every)
+        ctx.qsg_measure_correlators()
+        orc.measure()
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    gpu = ctx.qsg_read_correlators(raw=True)
+    _check_corr(gpu, orc.read())
+    assert ctx.qsg_get_counters() == (2000, 0, 200)
+
+
+def test_checkpoint_resume_is_bit_exact():
+    shape = Q.Shape(8, 16, 64, 2, 3, Q.METROPOLIS, Q.PBC)
+    lad = np.array([0.22, 0.28, 0.34])
+    a = Q.Context([shape])
+    a.qsg_init_samples(99, [lad])
+    a.qsg_sweep(4)
+    a.qsg_tempering_swap()
+    state = a.qsg_get_spins(0)
+    counters = a.qsg_get_counters()
+    a.qsg_sweep(5)
+    a.qsg_tempering_swap()
+    b = Q.Context([shape])
+    b.qsg_init_samples(99, [lad])
+    b.qsg_set_spins(0, state)
+    b.qsg_set_counters(*counters)
+    b.qsg_sweep(5)
+    b.qsg_tempering_swap()
+    assert np.array_equal(a.qsg_get_spins(0), b.qsg_get_spins(0))
+
+
+def _sampled_full_size(w, sweeps_before_swap, n_swaps, sample, configs):
+    """Full-size GPU run against one sample simulated alone by the oracle."""
+    shape, lad = w.shapes[0], w.ladders[0]
+    ctx = Q.Context([shape])
+    ctx.qsg_init_samples(w.seed, [lad])
+    orc = oracle.OracleGroup(shape.L, shape.Ltau, 1, shape.n_replicas, shape.n_k, algo=shape.algo,
+                             boundary=shape.boundary, first_sample=sample)
+    orc.init(w.seed, lad)
+    for _ in range(n_swaps):
+        ctx.qsg_sweep(sweeps_before_swap)
+        orc.sweep(sweeps_before_swap)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+    ctx.qsg_measure_correlators()
+    words = ctx.qsg_get_spins(0).reshape(shape.words, shape.n_replicas, shape.n_k, -1)
+    mine = (1 - 2 * ((words[sample // 64] >> np.uint64(sample % 64)) & np.uint64(1)).astype(np.int8))
+    assert np.array_equal(mine.reshape(orc.spins()[0].shape), orc.spins()[0])
+    assert np.array_equal(ctx.qsg_read_energies()[sample], orc.energies()[0])
+    assert np.array_equal(ctx.qsg_read_accepts()[sample], orc.accepts()[0])
+    gpu = ctx.qsg_read_correlators(raw=True)
+    for r, j in configs:
+        C, Qs = orc.measure_one(0, r, j)
+        assert np.array_equal(gpu["C_raw"][r, sample, j], C)
+        assert np.array_equal(gpu["Q2_raw"][r, sample, j], Qs)
+    # properties that hold for every sample at any size
+    assert np.all(gpu["C"][..., 0] == 1.0) and np.all(gpu["Q2"][..., 0] == 1.0)
+    assert np.all(np.abs(gpu["C"]) <= 1.0) and np.all((gpu["Q2"] >= 0) & (gpu["Q2"] <= 1.0))
+    assert np.all((gpu["q2"] >= 0) & (gpu["q2"] <= 1.0))
+
+
+def test_mid_scale_sampled():
+    w = workloads.mid_scale()
+    _sampled_full_size(w, 10, 2, sample=37, configs=[(0, 0), (3, 23)])
+
+
+def test_largest_sampled_in_bench_configuration():
+    w = workloads.largest()
+    _sampled_full_size(w, 2, 1, sample=77, configs=[(1, 5)])
