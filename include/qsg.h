@@ -24,8 +24,10 @@
  * (low word first).  Counters, with gid the group index:
  *   couplings   (n = y L + x, dir, w, 1<<24 | gid<<8): bits of out[0] | out[1]<<32
  *   hot start   (n, 0, slot, 2<<24 | gid<<8):           bits of out[0] | out[1]<<32
- *   sweep       (block, sweep, slot, 3<<24 | gid<<8): site (x, y, tau) takes
- *               out[(tau & 1) * 2 + (x & 1)] with block = ((tau/2) L + y)(L/2) + x/2;
+ *   sweep       (block, sweep, slot, 3<<24 | gid<<8): rows are cut into column
+ *               pairs starting at x = y & 1 (odd rows pair (1,2), ..., (L-1,0));
+ *               with xs = (x - (y & 1)) mod L, site (x, y, tau) takes
+ *               out[(tau & 1) * 2 + (xs & 1)], block = ((tau/2) L + y)(L/2) + xs/2;
  *               one 32-bit uniform per site, sweep and slot, shared by the 64
  *               samples of the word
  *   tempering   (16 i + b/4, swap index, w R + r, 4<<24 | gid<<8): sample bit b

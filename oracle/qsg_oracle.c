@@ -33,7 +33,9 @@
  *       so C(0) = Q2(0) = 1.
  *   R3  Q2(tau) uses (sum_x S_x,tau1 S_x,tau1+tau)^2 of one configuration.
  *   R5  colour (x+y+tau) mod 2; a sweep = colour 0 then colour 1.
- *   R6  Philox4x32-10 keyed (seed_lo, seed_hi); counters given below.
+ *   R6  Philox4x32-10 keyed (seed_lo, seed_hi); counters given below.  The
+ *       sweep cuts rows into column pairs starting at x = y & 1 and time into
+ *       pairs (2m, 2m+1); one call per 2 x 2 block feeds its four sites.
  *   R7  the sweep draws ONE 32-bit uniform per site and sweep, shared by the
  *       64 disorder samples that occupy one multispin word of the GPU store
  *       (samples 64w .. 64w+63).  Different replicas and ladder positions
@@ -312,15 +314,19 @@ static int local_field(const orc_group *g, const int8_t *S, const int8_t *J, int
     return h;
 }
 
-/* uniform of site (x,y,t) in sweep `sw` for slot s: the lattice is tiled by
- * blocks of 2 (x) by 2 (tau) sites; one Philox call per block, sweep and slot
- * yields four words, word (t&1)*2 + (x&1) belongs to the site. */
+/* uniform of site (x,y,t) in sweep `sw` for slot s: every row is cut into
+ * pairs of neighbouring columns, (0,1),(2,3),... in even rows and
+ * (1,2),(3,4),...,(L-1,0) in odd rows, and time into pairs (2m, 2m+1); each
+ * resulting block of 2 x 2 sites draws one Philox call per sweep and slot, and
+ * the site at column offset dx within its pair and time offset t&1 takes word
+ * (t&1)*2 + dx. */
 static uint32_t sweep_uniform(const orc_group *g, uint32_t s, uint32_t sw, int x, int y, int t)
 {
-    uint32_t block = (uint32_t)(((t / 2) * g->L + y) * (g->L / 2) + x / 2);
+    int shifted = (x - (y & 1) + g->L) % g->L; /* column counted from the pair start */
+    uint32_t block = (uint32_t)(((t / 2) * g->L + y) * (g->L / 2) + shifted / 2);
     uint32_t o[4];
     draw(g->seed, block, sw, s, (ORC_STREAM_SWEEP << 24) | ((uint32_t)g->group_id << 8), o);
-    return o[(t & 1) * 2 + (x & 1)];
+    return o[(t & 1) * 2 + (shifted & 1)];
 }
 
 static void half_sweep(orc_group *g, int b, int r, int j, int colour)

@@ -59,9 +59,11 @@ __global__ void k_half_sweep_ref(Group g, int colour, uint32_t sweep, uint32_t k
         const uint64_t jxp = Jx[y * L + x], jxm = Jx[y * L + xm], jyp = Jy[y * L + x], jym = Jy[ym * L + x];
         const uint64_t fp = (g.boundary == 1 && t == Lt - 1) ? ~0ull : 0ull;  // APBC wrap bond
         const uint64_t fm = (g.boundary == 1 && t == 0) ? ~0ull : 0ull;
-        const uint32_t block = (uint32_t)(((t >> 1) * L + y) * half + xh);
+        // column pairs start at x = y & 1 (so odd rows pair (1,2), ..., (L-1,0))
+        const int xs = x - (y & 1) < 0 ? L - 1 : x - (y & 1);
+        const uint32_t block = (uint32_t)(((t >> 1) * L + y) * half + (xs >> 1));
         const uint4 r = philox4x32_10(make_uint4(block, sweep, (uint32_t)s, tag), k0, k1);
-        const uint32_t u = pick(r, (t & 1) * 2 + (x & 1));
+        const uint32_t u = pick(r, (t & 1) * 2 + (xs & 1));
         const uint32_t *T = g.thr + j * 16;
         uint64_t b0, b1, b2;
         if (g.algo == 0) {
