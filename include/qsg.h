@@ -157,6 +157,16 @@ qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host);
 qsg_status qsg_get_counters(qsg_ctx *ctx, uint32_t *sweeps, uint32_t *swaps, int64_t *n_meas);
 qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64_t n_meas);
 
+/* Tuning options (apply to every group of the context):
+ *   QSG_OPT_SWEEP_KERNEL  0 = automatic, 1 = one thread per site and colour
+ *                         (two launches per sweep), 2 = fused tau-wavefront
+ *                         (one launch per sweep; needs L_tau % 4 == 0, L_tau >= 8)
+ *   QSG_OPT_CHUNK         tau planes per wavefront work unit (0 = automatic;
+ *                         otherwise a multiple of 4 that divides every L_tau)
+ * Results do not depend on the options: every kernel produces the same bits. */
+enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2 };
+qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
+
 /* Number of kernels this library has launched in this process (all contexts);
  * a diagnostic for benchmarks and for checking that the GPU path ran. */
 uint64_t qsg_kernel_launches(void);

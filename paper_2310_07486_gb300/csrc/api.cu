@@ -88,6 +88,7 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
         g.outC = (double *)take(sizeof(double) * nc);
         g.outQ = (double *)take(sizeof(double) * nc);
         g.outP = (double *)take(sizeof(double) * (size_t)g.W * 64 * g.K);
+        g.arrivals = (unsigned *)take(sizeof(unsigned) * (size_t)g.nslots * (g.Ltau / 4 > 0 ? g.Ltau / 4 : 1));
         // one (w, j) pair at least, up to the cap
         const size_t per = measure_scratch_words_per_pair(g);
         size_t want = kScratchCap / sizeof(uint64_t);
@@ -134,6 +135,8 @@ struct qsg_ctx {
     bool energy_fresh = false;
     uint32_t sweeps = 0, swaps = 0;
     long long n_meas = 0;
+    int sweep_kernel = 0;  // QSG_OPT_SWEEP_KERNEL
+    int chunk = 0;         // QSG_OPT_CHUNK
     std::string last_cuda;
 };
 
@@ -188,6 +191,10 @@ qsg_status qsg_create(qsg_ctx **out, const qsg_shape *shapes, int32_t n_groups, 
     carve(c->groups, c->ws, &c->d_err, &c->scratch, &c->scratch_words);
     c->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream);
+    for (const Group &g : c->groups)
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(g.arrivals, 0, sizeof(unsigned) * (size_t)g.nslots * (g.Ltau / 4 > 0 ? g.Ltau / 4 : 1),
+                                c->stream);
     if (e != cudaSuccess) {
         delete c;
         return QSG_ERR_CUDA;
@@ -299,7 +306,13 @@ qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
     if (!ctx->initialised) return QSG_ERR_STATE;
     if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
     for (int it = 0; it < n_sweeps; ++it) {
-        for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_sweep_reference(g, ctx->sweeps, ctx->seed, ctx->stream));
+        for (const Group &g : ctx->groups) {
+            const int C = ctx->sweep_kernel == 1 ? 0 : wavefront_chunk(g, ctx->chunk);
+            if (C > 0)
+                QSG_CUDA(ctx, launch_sweep_wavefront(g, ctx->sweeps, ctx->seed, g.arrivals, C, ctx->stream));
+            else
+                QSG_CUDA(ctx, launch_sweep_reference(g, ctx->sweeps, ctx->seed, ctx->stream));
+        }
         ctx->sweeps++;
     }
     if (n_sweeps > 0) ctx->energy_fresh = false;
@@ -434,6 +447,27 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
     ctx->swaps = swaps;
     if (n_meas >= 0) ctx->n_meas = n_meas;
     return QSG_OK;
+}
+
+qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (option == QSG_OPT_SWEEP_KERNEL) {
+        if (value < 0 || value > 2) return QSG_ERR_ARG;
+        if (value == 2)
+            for (const Group &g : ctx->groups)
+                if (wavefront_chunk(g, ctx->chunk) == 0) return QSG_ERR_ARG;
+        ctx->sweep_kernel = (int)value;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_CHUNK) {
+        if (value < 0 || value > 65536) return QSG_ERR_ARG;
+        if (value > 0)
+            for (const Group &g : ctx->groups)
+                if (wavefront_chunk(g, (int)value) == 0) return QSG_ERR_ARG;
+        ctx->chunk = (int)value;
+        return QSG_OK;
+    }
+    return QSG_ERR_ARG;
 }
 
 uint64_t qsg_kernel_launches(void) { return (uint64_t)g_launches.load(); }

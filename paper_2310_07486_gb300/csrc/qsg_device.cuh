@@ -31,6 +31,7 @@ struct Group {
     long long *Cacc, *Qacc;   // [R][W*64][K][nlag]
     long long *Pacc;          // [W*64][K]
     double *outC, *outQ, *outP;
+    unsigned *arrivals;  // [nslots][L_tau/4] boundary arrival counters of the wavefront sweep
 };
 
 // ---------------------------------------------------------------------------

@@ -20,6 +20,12 @@ cudaError_t launch_init_spins(const Group &g, uint64_t seed, cudaStream_t st);
 // The "reference" variant runs one launch per colour with one thread per site.
 cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed, cudaStream_t st);
 
+// The fused wavefront sweep: C = planes per work unit (0 if the group cannot
+// use this kernel), arrivals = nslots * (L_tau / 4) zeroed counters.
+int wavefront_chunk(const Group &g, int requested);
+cudaError_t launch_sweep_wavefront(const Group &g, uint32_t sweep, uint64_t seed, unsigned *arrivals, int C,
+                                   cudaStream_t st);
+
 // Unsatisfied-bond counts U[slot][bit] of the current configurations.
 cudaError_t launch_energy(const Group &g, cudaStream_t st);
 

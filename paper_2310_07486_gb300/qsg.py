@@ -19,6 +19,8 @@ _lib = None
 
 METROPOLIS, HEATBATH = 0, 1
 PBC, APBC = 0, 1
+OPT_SWEEP_KERNEL, OPT_CHUNK = 1, 2
+SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "invalid group shape", -3: "CUDA runtime error",
           -4: "bounded device wait gave up", -5: "call out of order", -6: "workspace missing or too small"}
@@ -79,6 +81,8 @@ def load_library(path: str | None = None):
     lib.qsg_get_counters.argtypes = [vp, vp, vp, vp]
     lib.qsg_set_counters.restype = i32
     lib.qsg_set_counters.argtypes = [vp, u32, u32, ctypes.c_int64]
+    lib.qsg_set_option.restype = i32
+    lib.qsg_set_option.argtypes = [vp, i32, ctypes.c_int64]
     lib.qsg_kernel_launches.restype = ctypes.c_uint64
     lib.qsg_kernel_launches.argtypes = []
     lib.qsg_strerror.restype = ctypes.c_char_p
@@ -93,7 +97,7 @@ def exported_symbols():
     return ["qsg_workspace_bytes", "qsg_create", "qsg_destroy", "qsg_set_stream", "qsg_init_samples",
             "qsg_set_couplings", "qsg_sweep", "qsg_tempering_swap", "qsg_measure_correlators",
             "qsg_read_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
-            "qsg_get_counters", "qsg_set_counters", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
+            "qsg_get_counters", "qsg_set_counters", "qsg_set_option", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
 
 
 def qsg_kernel_launches() -> int:
@@ -251,6 +255,9 @@ class Context:
                     "qsg_get_counters")
         return a.value, b.value, c.value
 
+
+    def qsg_set_option(self, option, value):
+        self._check(self.lib.qsg_set_option(self.h, int(option), int(value)), "qsg_set_option")
 
     def qsg_set_counters(self, sweeps, swaps, n_meas=-1):
         self._check(self.lib.qsg_set_counters(self.h, int(sweeps), int(swaps), int(n_meas)), "qsg_set_counters")

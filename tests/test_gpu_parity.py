@@ -210,3 +210,38 @@ def test_mid_scale_sampled():
 def test_largest_sampled_in_bench_configuration():
     w = workloads.largest()
     _sampled_full_size(w, 2, 1, sample=77, configs=[(1, 5)])
+
+
+@pytest.mark.parametrize("L,Ltau,chunk", [(8, 16, 4), (8, 16, 8), (8, 16, 16), (6, 32, 8), (24, 16, 4), (2, 8, 4),
+                                          (32, 8, 8), (10, 24, 12), (4, 64, 0)])
+@pytest.mark.parametrize("algo,boundary", [(Q.METROPOLIS, Q.PBC), (Q.HEATBATH, Q.APBC)])
+def test_wavefront_sweep_matches_oracle(L, Ltau, chunk, algo, boundary):
+    """The fused one-pass sweep (chunked tau wavefront with deferred boundary
+    planes) against the oracle, for several chunk lengths and block shapes."""
+    shape = Q.Shape(L, Ltau, 70, 2, 2, algo, boundary)
+    ctx, orc = _pair(shape, np.array([0.26, 0.32]), seed=31)
+    ctx.qsg_set_option(Q.OPT_SWEEP_KERNEL, Q.SWEEP_WAVEFRONT)
+    ctx.qsg_set_option(Q.OPT_CHUNK, chunk)
+    for n in (1, 3):
+        ctx.qsg_sweep(n)
+        orc.sweep(n)
+        assert np.array_equal(_gpu_spins(ctx, shape), orc.spins()), n
+    ctx.qsg_tempering_swap()
+    orc.swap()
+    ctx.qsg_sweep(2)
+    orc.sweep(2)
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+
+
+def test_reference_and_wavefront_kernels_agree_at_mid_scale():
+    w = workloads.mid_scale()
+    out = []
+    for kern in (Q.SWEEP_REFERENCE, Q.SWEEP_WAVEFRONT):
+        ctx = Q.Context(w.shapes)
+        ctx.qsg_init_samples(w.seed, w.ladders)
+        ctx.qsg_set_option(Q.OPT_SWEEP_KERNEL, kern)
+        ctx.qsg_sweep(5)
+        ctx.qsg_tempering_swap()
+        ctx.qsg_sweep(5)
+        out.append(ctx.qsg_get_spins(0))
+    assert np.array_equal(out[0], out[1])
