@@ -163,8 +163,12 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         (one launch per sweep; needs L_tau % 4 == 0, L_tau >= 8)
  *   QSG_OPT_CHUNK         tau planes per wavefront work unit (0 = automatic;
  *                         otherwise a multiple of 4 that divides every L_tau)
+ *   QSG_OPT_WAVEFRONT_VARIANT  0 = one slot per thread, 2 blocks per SM;
+ *                         1 = two replicas per thread (needs an even R);
+ *                         2 = one slot per thread, 3 blocks per SM;
+ *                         process-wide
  * Results do not depend on the options: every kernel produces the same bits. */
-enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2 };
+enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Number of kernels this library has launched in this process (all contexts);

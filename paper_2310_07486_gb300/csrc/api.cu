@@ -459,6 +459,11 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         ctx->sweep_kernel = (int)value;
         return QSG_OK;
     }
+    if (option == QSG_OPT_WAVEFRONT_VARIANT) {
+        if (value < 0 || value > 2) return QSG_ERR_ARG;
+        g_wavefront_variant = (int)value;
+        return QSG_OK;
+    }
     if (option == QSG_OPT_CHUNK) {
         if (value < 0 || value > 65536) return QSG_ERR_ARG;
         if (value > 0)

@@ -23,6 +23,7 @@ cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed
 // The fused wavefront sweep: C = planes per work unit (0 if the group cannot
 // use this kernel), arrivals = nslots * (L_tau / 4) zeroed counters.
 int wavefront_chunk(const Group &g, int requested);
+extern int g_wavefront_variant;  // 0: register cap for 3 blocks/SM when blocks <= 288 threads; 1: 2 blocks/SM
 cudaError_t launch_sweep_wavefront(const Group &g, uint32_t sweep, uint64_t seed, unsigned *arrivals, int C,
                                    cudaStream_t st);
 

@@ -19,7 +19,7 @@ _lib = None
 
 METROPOLIS, HEATBATH = 0, 1
 PBC, APBC = 0, 1
-OPT_SWEEP_KERNEL, OPT_CHUNK = 1, 2
+OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT = 1, 2, 3
 SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "invalid group shape", -3: "CUDA runtime error",

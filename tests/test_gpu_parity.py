@@ -245,3 +245,20 @@ def test_reference_and_wavefront_kernels_agree_at_mid_scale():
         ctx.qsg_sweep(5)
         out.append(ctx.qsg_get_spins(0))
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("L,R,algo", [(8, 2, Q.HEATBATH), (24, 2, Q.METROPOLIS), (24, 3, Q.HEATBATH),
+                                      (32, 2, Q.HEATBATH), (6, 4, Q.METROPOLIS)])
+def test_wavefront_register_variants_match_oracle(variant, L, R, algo):
+    """Every kernel variant (one or two replicas per thread, register budgets)
+    gives the oracle's bits."""
+    shape = Q.Shape(L, 16, 70, R, 2, algo, Q.APBC)
+    ctx, orc = _pair(shape, np.array([0.27, 0.3]), seed=41)
+    ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, variant)
+    try:
+        ctx.qsg_sweep(3)
+        orc.sweep(3)
+        assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    finally:
+        ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, 0)
