@@ -160,12 +160,11 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
 /* Tuning options (apply to every group of the context):
  *   QSG_OPT_SWEEP_KERNEL  0 = automatic, 1 = one thread per site and colour
  *                         (two launches per sweep), 2 = fused tau-wavefront
- *                         (one launch per sweep; needs L_tau % 4 == 0, L_tau >= 8)
+ *                         (one launch per sweep; needs L_tau % 8 == 0)
  *   QSG_OPT_CHUNK         tau planes per wavefront work unit (0 = automatic;
- *                         otherwise a multiple of 4 that divides every L_tau)
- *   QSG_OPT_WAVEFRONT_VARIANT  0 = one slot per thread, 2 blocks per SM;
- *                         1 = two replicas per thread (needs an even R);
- *                         2 = one slot per thread, 3 blocks per SM;
+ *                         otherwise a multiple of 8 that divides every L_tau)
+ *   QSG_OPT_WAVEFRONT_VARIANT  register budget of the wavefront kernel:
+ *                         0 = two blocks per SM, 1 = three blocks per SM;
  *                         process-wide
  * Results do not depend on the options: every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3 };

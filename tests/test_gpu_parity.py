@@ -212,8 +212,9 @@ def test_largest_sampled_in_bench_configuration():
     _sampled_full_size(w, 2, 1, sample=77, configs=[(1, 5)])
 
 
-@pytest.mark.parametrize("L,Ltau,chunk", [(8, 16, 4), (8, 16, 8), (8, 16, 16), (6, 32, 8), (24, 16, 4), (2, 8, 4),
-                                          (32, 8, 8), (10, 24, 12), (4, 64, 0)])
+@pytest.mark.parametrize("L,Ltau,chunk", [(8, 16, 16), (8, 32, 16), (8, 64, 32), (8, 32, 0), (6, 32, 16),
+                                          (24, 16, 16), (2, 16, 16), (32, 16, 16), (10, 48, 16), (4, 64, 0),
+                                          (12, 48, 16), (16, 96, 32), (20, 32, 16)])
 @pytest.mark.parametrize("algo,boundary", [(Q.METROPOLIS, Q.PBC), (Q.HEATBATH, Q.APBC)])
 def test_wavefront_sweep_matches_oracle(L, Ltau, chunk, algo, boundary):
     """The fused one-pass sweep (chunked tau wavefront with deferred boundary
@@ -247,7 +248,7 @@ def test_reference_and_wavefront_kernels_agree_at_mid_scale():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1])
 @pytest.mark.parametrize("L,R,algo", [(8, 2, Q.HEATBATH), (24, 2, Q.METROPOLIS), (24, 3, Q.HEATBATH),
                                       (32, 2, Q.HEATBATH), (6, 4, Q.METROPOLIS)])
 def test_wavefront_register_variants_match_oracle(variant, L, R, algo):
