@@ -166,8 +166,11 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *   QSG_OPT_WAVEFRONT_VARIANT  register budget of the wavefront kernel:
  *                         0 = two blocks per SM, 1 = three blocks per SM;
  *                         process-wide
+ *   QSG_OPT_CORR_KERNEL   0 = tensor cores (Gram tiles by tcgen05.mma in FP8,
+ *                         exact for +-1 spins), 1 = XOR/popcount on the
+ *                         integer pipes
  * Results do not depend on the options: every kernel produces the same bits. */
-enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3 };
+enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Number of kernels this library has launched in this process (all contexts);

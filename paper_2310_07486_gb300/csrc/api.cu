@@ -137,6 +137,7 @@ struct qsg_ctx {
     long long n_meas = 0;
     int sweep_kernel = 0;  // QSG_OPT_SWEEP_KERNEL
     int chunk = 0;         // QSG_OPT_CHUNK
+    int corr_tensor = 1;   // QSG_OPT_CORR_KERNEL: 1 tensor cores, 0 integer pipes
     std::string last_cuda;
 };
 
@@ -339,7 +340,8 @@ qsg_status qsg_tempering_swap(qsg_ctx *ctx) {
 qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
-    for (const Group &g : ctx->groups) QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->stream));
+    for (const Group &g : ctx->groups)
+        QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->corr_tensor, ctx->d_err, ctx->stream));
     ctx->n_meas++;
     return QSG_OK;
 }
@@ -462,6 +464,11 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
     if (option == QSG_OPT_WAVEFRONT_VARIANT) {
         if (value < 0 || value > 1) return QSG_ERR_ARG;
         g_wavefront_variant = (int)value;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_CORR_KERNEL) {
+        if (value < 0 || value > 1) return QSG_ERR_ARG;
+        ctx->corr_tensor = value == 0 ? 1 : 0;
         return QSG_OK;
     }
     if (option == QSG_OPT_CHUNK) {

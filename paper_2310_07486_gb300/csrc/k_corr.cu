@@ -119,14 +119,15 @@ __global__ void __launch_bounds__(256) k_overlap(Group g, int p0, const uint64_t
     }
 }
 
-cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, cudaStream_t st) {
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int *status,
+                           cudaStream_t st) {
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
     if (batch < 1) return cudaErrorInvalidValue;
     const int npairs_total = g.W * g.K;
     const size_t sh_bytes = (size_t)g.Ltau * g.nwx * sizeof(uint64_t);
     const int use_smem = sh_bytes <= 200 * 1024 ? 1 : 0;
-    if (use_smem) {
+    if (use_smem && !tensor) {
         cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh_bytes);
         if (e != cudaSuccess) return e;
     }
@@ -137,9 +138,13 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
         k_transpose<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, p0, np, scratch);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
-        count_launches(1);
-        k_gram<<<np * g.R * 64, 256, use_smem ? sh_bytes : 0, st>>>(g, p0, scratch, use_smem);
-        e = cudaGetLastError();
+        if (tensor) {
+            e = launch_gram_tc(g, p0, np, scratch, status, st);
+        } else {
+            count_launches(1);
+            k_gram<<<np * g.R * 64, 256, use_smem ? sh_bytes : 0, st>>>(g, p0, scratch, use_smem);
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) return e;
         if (g.R >= 2) {
             count_launches(1);

@@ -33,8 +33,13 @@ cudaError_t launch_energy(const Group &g, cudaStream_t st);
 // Tempering step `m`: decisions (and U bookkeeping), then the spin-bit moves.
 cudaError_t launch_tempering(const Group &g, uint32_t m, uint64_t seed, cudaStream_t st);
 
-// Correlator accumulation through the x-packed transposed scratch buffer.
-cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, cudaStream_t st);
+// Correlator accumulation through the x-packed transposed scratch buffer;
+// tensor = 1 computes the Gram tiles with tcgen05 (k_corr_tc.cu), 0 with
+// XOR/popcount on the integer pipes.  status receives DEVERR_TIMEOUT if a
+// bounded wait of the tensor path gave up.
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int *status,
+                           cudaStream_t st);
+cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st);
 
 // FP64 finish into g.outC / g.outQ / g.outP.
 cudaError_t launch_finish(const Group &g, long long n_meas, cudaStream_t st);

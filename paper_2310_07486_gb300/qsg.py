@@ -19,7 +19,8 @@ _lib = None
 
 METROPOLIS, HEATBATH = 0, 1
 PBC, APBC = 0, 1
-OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT = 1, 2, 3
+OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL = 1, 2, 3, 4
+CORR_TENSOR, CORR_INTEGER = 0, 1
 SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "invalid group shape", -3: "CUDA runtime error",
