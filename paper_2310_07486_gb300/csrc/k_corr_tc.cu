@@ -58,43 +58,61 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-// 8 bits -> 8 bytes with 0x80 in the bytes whose bit is set
-__device__ __forceinline__ uint64_t spread8(const uint64_t *lut, uint32_t bits) { return lut[bits & 0xFF]; }
-
 }  // namespace
 
-// grid: (row blocks nb, slots-bits of the batch); P: [slot_b][bit][Ltau][nwx]
+// 4 bits -> 4 bytes: byte k = 0x80 if bit k is set (isolate bit k in byte k,
+// then carry it to the top of the byte).
+__device__ __forceinline__ uint32_t spread4(uint32_t x) {
+    const uint32_t y = ((x & 0xFu) * 0x01010101u) & 0x08040201u;
+    return (y + 0x7F7F7F7Fu) & 0x80808080u;
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+
+// grid: (row blocks nb, slot-bits of the batch); P: [slot_b][bit][Ltau][nwx].
+// Shared memory: operand chunks [2 buffers][A, B][16 KB] (1024-aligned), the
+// lag bins, and the bit rows of the A block and of two B blocks (the next one
+// is fetched while the current one is multiplied).
 __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nb,
                                                       int *status) {
     extern __shared__ __align__(16) uint8_t dyn_raw[];
-    // the 128-byte swizzle wants 1024-byte aligned operand chunks
     uint8_t *dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
-    uint8_t *sbuf = dyn;                                   // [2 buffers][A, B][16 KB]
-    uint64_t *lut = reinterpret_cast<uint64_t *>(dyn + 4 * kChunkBytes);   // 256 entries
-    int *binC = reinterpret_cast<int *>(lut + 256);        // [nlag]
-    int *binQ = binC + g.nlag;                             // [nlag]
+    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L, half = Lt / 2;
+    uint8_t *sbuf = dyn;
+    int *binC = reinterpret_cast<int *>(dyn + 4 * kChunkBytes);
+    int *binQ = binC + g.nlag;
+    uint64_t *bitsA = reinterpret_cast<uint64_t *>(binQ + g.nlag);
+    bitsA = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(bitsA) + 15) & ~(uintptr_t)15);
+    uint64_t *bitsB = bitsA + kTile * nwx;  // [2][kTile][nwx]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
-    __shared__ int abort_flag;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i = blockIdx.x;                 // row block
-    const int sbb = blockIdx.y;               // (slot of batch, bit)
+    const int i = blockIdx.x;
+    const int sbb = blockIdx.y;
     const int sb = sbb / 64, bit = sbb % 64;
     const int pb = sb / g.R, r = sb % g.R;
     const int pidx = p0 + pb, w = pidx / g.K, j = pidx % g.K;
-    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L, half = Lt / 2;
     const int nchunks = (L2 + kChunk - 1) / kChunk;
     const uint64_t *src = P + ((size_t)sb * 64 + bit) * Lt * nwx;
 
-    for (int v = tid; v < 256; v += kThreads) {
-        uint64_t x = 0;
-        for (int q = 0; q < 8; ++q)
-            if (v >> q & 1) x |= 0x80ull << (8 * q);
-        lut[v] = x;
-    }
+    // bit rows of block blk into dst (one row per thread; rows past L_tau are zero)
+    auto fetch_rows = [&](uint64_t *dst, int blk) {
+        const int t = blk * kTile + tid;
+        uint64_t *d = dst + tid * nwx;
+        if (t < Lt) {
+            for (int x = 0; x < nwx; ++x) cp_async8(d + x, src + (size_t)t * nwx + x);
+        } else {
+            for (int x = 0; x < nwx; ++x) d[x] = 0ull;
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    fetch_rows(bitsA, i);
+    fetch_rows(bitsB, i);
     for (int l = tid; l < g.nlag; l += kThreads) binC[l] = binQ[l] = 0;
-    if (tid == 0) abort_flag = 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&tmem_slot)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
@@ -104,50 +122,63 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
     }
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = idesc_e4m3_128x128();
 
-    // expand rows [blk*128, blk*128+128) of K chunk kc into a swizzled operand chunk
-    auto expand = [&](uint8_t *dst, int blk, int kc) {
-        const int row = tid;                      // one row per thread
+    // expand K chunk kc of the bit rows `bits` into a swizzled E4M3 operand chunk
+    auto expand = [&](uint8_t *dst, const uint64_t *bits, int blk, int kc) {
+        const int row = tid;
         const int t = blk * kTile + row;
         const int k0 = kc * kChunk;
-        uint64_t wlo = 0, whi = 0;
-        int valid = 0;
-        if (t < Lt) {
-            const int w0 = k0 / 64;
-            wlo = w0 < nwx ? src[(size_t)t * nwx + w0] : 0ull;
-            whi = w0 + 1 < nwx ? src[(size_t)t * nwx + w0 + 1] : 0ull;
-            valid = min(max(L2 - k0, 0), kChunk);
-        }
+        const int w0 = k0 / 64;
+        const uint64_t *b = bits + row * nwx;
+        const uint64_t wlo = w0 < nwx ? b[w0] : 0ull;
+        const uint64_t whi = w0 + 1 < nwx ? b[w0 + 1] : 0ull;
+        const int valid = t < Lt ? min(max(L2 - k0, 0), kChunk) : 0;
         uint8_t *rowp = dst + row * 128;
+        // E4M3: +1 = 0x38, -1 = 0xB8 (set bit = spin -1), 0 for padding sites
+        if (valid == kChunk) {
 #pragma unroll
-        for (int c16 = 0; c16 < 8; ++c16) {
-            const uint64_t wsrc = c16 < 4 ? wlo : whi;
-            const int sh = (c16 & 3) * 16;
-            const uint32_t b16 = (uint32_t)(wsrc >> sh) & 0xFFFFu;
-            // validity of the 16 sites of this 16-byte chunk
-            const int nv = min(max(valid - c16 * 16, 0), 16);
-            const uint32_t v16 = nv >= 16 ? 0xFFFFu : ((1u << nv) - 1u);
-            const uint64_t lo = (spread8(lut, b16) | 0x3838383838383838ull) & ((spread8(lut, v16) >> 7) * 0xFFull);
-            const uint64_t hi = (spread8(lut, b16 >> 8) | 0x3838383838383838ull) & ((spread8(lut, v16 >> 8) >> 7) * 0xFFull);
-            *reinterpret_cast<ulonglong2 *>(rowp + ((c16 ^ (row & 7)) << 4)) = make_ulonglong2(lo, hi);
+            for (int c16 = 0; c16 < 8; ++c16) {
+                const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
+                const uint4 v = make_uint4(spread4(b16) | 0x38383838u, spread4(b16 >> 4) | 0x38383838u,
+                                           spread4(b16 >> 8) | 0x38383838u, spread4(b16 >> 12) | 0x38383838u);
+                *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = v;
+            }
+        } else {
+#pragma unroll
+            for (int c16 = 0; c16 < 8; ++c16) {
+                const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
+                const int nv = min(max(valid - c16 * 16, 0), 16);
+                const uint32_t v16 = nv >= 16 ? 0xFFFFu : ((1u << nv) - 1u);
+                uint32_t out[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const uint32_t keep = (spread4(v16 >> (4 * qq)) >> 7) * 0xFFu;
+                    out[qq] = (spread4(b16 >> (4 * qq)) | 0x38383838u) & keep;
+                }
+                *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = make_uint4(out[0], out[1], out[2], out[3]);
+            }
         }
     };
 
     uint32_t phase[2] = {0, 0};
-    int issued[2] = {0, 0};   // commits outstanding per buffer
-    int gchunk = 0;           // running chunk index (buffer = gchunk & 1)
+    int issued[2] = {0, 0};
+    int gchunk = 0;
     bool ok = true;
+    const int m = warp * 32 + lane;  // TMEM lane = tile row
+    const int t1 = i * kTile + m;
 
     for (int jb = i; jb < nb && ok; ++jb) {
+        const uint64_t *bb = bitsB + (size_t)((jb - i) & 1) * kTile * nwx;
+        // fetch the next B block while this one is multiplied
+        if (jb + 1 < nb) fetch_rows(bitsB + (size_t)((jb + 1 - i) & 1) * kTile * nwx, jb + 1);
         for (int kc = 0; kc < nchunks; ++kc, ++gchunk) {
             const int buf = gchunk & 1;
-            // the MMA that last read this buffer must be complete; every thread
-            // waits and the block agrees on the outcome before going on
             bool mine = true;
             if (issued[buf]) {
                 mine = mbar_wait(smem_u32(&mbar[buf]), phase[buf]);
@@ -157,8 +188,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
             ok = __syncthreads_and(mine) != 0;
             if (!ok) break;
             uint8_t *sA = sbuf + buf * 2 * kChunkBytes, *sB = sA + kChunkBytes;
-            expand(sA, i, kc);
-            expand(sB, jb, kc);
+            expand(sA, bitsA, i, kc);
+            expand(sB, bb, jb, kc);
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncthreads();
             if (tid == 0) {
@@ -178,7 +209,6 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
             issued[buf] = 1;
         }
         if (!ok) break;
-        // wait for the tile's last MMA, then fold the accumulator into the lag bins
         const int lastbuf = (gchunk - 1) & 1;
         const bool mine = mbar_wait(smem_u32(&mbar[lastbuf]), phase[lastbuf]);
         phase[lastbuf] ^= 1u;
@@ -186,8 +216,14 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
         ok = __syncthreads_and(mine) != 0;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;\n");
-        const int m = warp * 32 + lane;       // TMEM lane = row of the tile
-        const int t1 = i * kTile + m;
+        // offsets o = t2 - t1 of this tile lie in [omin, omax]; most tiles map
+        // every element to lag o (all o < L_tau/2) or to lag L_tau - o (all o >
+        // L_tau/2), only the tiles around L_tau/2 need the per-element choice
+        const int obase = (jb - i) * kTile;
+        const int omin = jb == i ? 1 : obase - (kTile - 1), omax = obase + kTile - 1;
+        const bool full = (jb + 1) * kTile <= Lt && (i + 1) * kTile <= Lt;
+        const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
+        const int whigh = g.boundary == 1 ? -1 : 1;
 #pragma unroll 1
         for (int c0 = 0; c0 < kTile; c0 += 16) {
             uint32_t v[16];
@@ -198,11 +234,26 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            if (t1 < Lt) {
+            const int o0 = obase + c0 - m;  // offset of column q is o0 + q
+            if (full && cls == 0 && jb != i) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int gv = __float2int_rn(__uint_as_float(v[q]));
+                    atomicAdd(&binC[o0 + q], gv);
+                    atomicAdd(&binQ[o0 + q], gv * gv);
+                }
+            } else if (full && cls == 1) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int gv = __float2int_rn(__uint_as_float(v[q]));
+                    atomicAdd(&binC[Lt - o0 - q], whigh * gv);
+                    atomicAdd(&binQ[Lt - o0 - q], gv * gv);
+                }
+            } else if (t1 < Lt) {
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     const int t2 = jb * kTile + c0 + q;
-                    const int o = t2 - t1;
+                    const int o = o0 + q;
                     if (t2 < Lt && o > 0) {
                         const int gv = __float2int_rn(__uint_as_float(v[q]));
                         int lag, wc, wq;
@@ -211,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
                         } else if (o == half) {
                             lag = half; wc = g.boundary == 1 ? 0 : 2; wq = 2;
                         } else {
-                            lag = Lt - o; wc = g.boundary == 1 ? -1 : 1; wq = 1;
+                            lag = Lt - o; wc = whigh; wq = 1;
                         }
                         atomicAdd(&binC[lag], wc * gv);
                         atomicAdd(&binQ[lag], wq * gv * gv);
@@ -219,17 +270,18 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
                 }
             }
         }
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;\n");
-        __syncthreads();   // the next tile's first MMA overwrites the accumulator
+        __syncthreads();  // next B rows visible; the next tile may overwrite the accumulator
     }
-    if (!ok && tid == 0) atomicExch(&abort_flag, 1);
-    // drain: make sure no MMA is still reading shared memory or writing TMEM
+    const bool failed = !ok;
     for (int b = 0; b < 2; ++b)
         if (issued[b]) mbar_wait(smem_u32(&mbar[b]), phase[b]);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
-    if (abort_flag) {
+    if (failed) {
         if (tid == 0) atomicExch(status, DEVERR_TIMEOUT);
         return;
     }
@@ -247,7 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
 }
 
 size_t gram_tc_smem_bytes(const Group &g) {
-    return 1024 + 4 * (size_t)kChunkBytes + 256 * sizeof(uint64_t) + 2 * sizeof(int) * (size_t)g.nlag;
+    return 1024 + 4 * (size_t)kChunkBytes + 2 * sizeof(int) * (size_t)g.nlag + 16 +
+           3 * (size_t)kTile * g.nwx * sizeof(uint64_t);
 }
 
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st) {
