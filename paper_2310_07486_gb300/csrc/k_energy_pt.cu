@@ -4,68 +4,114 @@
 
 namespace qsg {
 
-// Add one word to a bitsliced vertical counter (plane p holds bit p of the
-// per-position counts); the carry chain stops as soon as no position carries.
-template <int P>
-__device__ __forceinline__ void vadd(uint64_t (&c)[P], uint64_t x) {
+constexpr int kEnergyPlanes = 16;
+constexpr int kEnergyRun = 240;  // tau planes per thread (a multiple of kFlush)
+constexpr int kFlush = 5;       // planes between flushes of the 4-bit accumulator (5 * 3 <= 15)
+
+// a += b for two bitsliced counters of kEnergyPlanes planes (ripple carry)
+__device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const uint64_t (&b)[kEnergyPlanes]) {
+    uint64_t carry = 0;
 #pragma unroll
-    for (int p = 0; p < P; ++p) {
-        const uint64_t t = c[p] & x;
-        c[p] ^= x;
-        x = t;
-        if (!x) break;
+    for (int p = 0; p < kEnergyPlanes; ++p) {
+        const uint64_t s = a[p] ^ b[p] ^ carry;
+        carry = (a[p] & b[p]) | (carry & (a[p] ^ b[p]));
+        a[p] = s;
     }
 }
 
-constexpr int kEnergyPlanes = 16;
-constexpr int kEnergyThreads = 256;
-
 // U[slot][b] += number of unsatisfied bonds (J S S' = -1) among the three
-// forward bonds (+x, +y, +tau) of every site in this block's chunk.  Each bond
-// is counted once; E = -(3N - 2U) is the action of Eq. (Trotter-action).
-__global__ void __launch_bounds__(kEnergyThreads) k_energy(Group g, int sites_per_block) {
+// forward bonds (+x, +y, +tau) of every site; each bond is counted once and
+// E = -(3N - 2U) is the action of Eq. (Trotter-action).  One thread per site
+// of a plane walks kEnergyRun planes with coalesced loads.  The three bond
+// words of a site go through a full adder into a 4-bit carry-save
+// accumulator (ones, twos, fours, eights), which is added into the 8-plane
+// per-thread counter every kFlush planes; the warp then sums its counters
+// with shuffles and one lane turns them into per-sample integers.
+__global__ void __launch_bounds__(256) k_energy(Group g) {
     __shared__ int cnt[64];
     const int s = blockIdx.y;
     const int L = g.L, L2 = L * L, Lt = g.Ltau;
     const int w = s / (g.R * g.K);
     const uint64_t *S = g.S + (size_t)s * g.N;
-    const uint64_t *Jx = g.Jx + (size_t)w * L2, *Jy = g.Jy + (size_t)w * L2;
-    if (threadIdx.x < 64) cnt[threadIdx.x] = 0;
+    for (int b = threadIdx.x; b < 64; b += blockDim.x) cnt[b] = 0;
     __syncthreads();
     uint64_t c[kEnergyPlanes];
 #pragma unroll
     for (int p = 0; p < kEnergyPlanes; ++p) c[p] = 0;
-    const int n0 = blockIdx.x * sites_per_block;
-    const int n1 = min(n0 + sites_per_block, g.N);
-    for (int n = n0 + threadIdx.x; n < n1; n += blockDim.x) {
-        const int t = n / L2, xy = n % L2, y = xy / L, x = xy % L;
-        const uint64_t v = S[n];
-        const uint64_t vx = S[t * L2 + y * L + (x + 1 == L ? 0 : x + 1)];
-        const uint64_t vy = S[t * L2 + (y + 1 == L ? 0 : y + 1) * L + x];
-        const uint64_t vt = S[(t + 1 == Lt ? 0 : t + 1) * L2 + xy];
-        const uint64_t ft = (g.boundary == 1 && t == Lt - 1) ? ~0ull : 0ull;
-        vadd(c, v ^ vx ^ Jx[xy]);
-        vadd(c, v ^ vy ^ Jy[xy]);
-        vadd(c, v ^ vt ^ ft);
-    }
-    for (int b = 0; b < 64; ++b) {
-        int v = 0;
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;  // site within a plane (grid.x covers L^2)
+    const int t0 = blockIdx.z * kEnergyRun, t1 = min(t0 + kEnergyRun, Lt);
+    if (xy < L2) {
+        const int y = xy / L, x = xy - y * L;
+        const int xr = y * L + (x + 1 == L ? 0 : x + 1), yu = (y + 1 == L ? 0 : y + 1) * L + x;
+        const uint64_t jx = g.Jx[(size_t)w * L2 + xy], jy = g.Jy[(size_t)w * L2 + xy];
+        for (int tb = t0; tb < t1; tb += kFlush) {
+            uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0;
 #pragma unroll
-        for (int p = 0; p < kEnergyPlanes; ++p) v |= (int)((c[p] >> b) & 1ull) << p;
-        if (v) atomicAdd(&cnt[b], v);
+            for (int k = 0; k < kFlush; ++k) {
+                const int t = tb + k;
+                if (t < t1) {
+                    const uint64_t *P = S + (size_t)t * L2;
+                    const int tn = t + 1 == Lt ? 0 : t + 1;
+                    const uint64_t v = __ldg(P + xy);
+                    const uint64_t vt = __ldg(S + (size_t)tn * L2 + xy);
+                    const uint64_t ft = (g.boundary == 1 && t == Lt - 1) ? ~0ull : 0ull;
+                    const uint64_t ux = v ^ __ldg(P + xr) ^ jx, uy = v ^ __ldg(P + yu) ^ jy, ut = v ^ vt ^ ft;
+                    const uint64_t sum = ux ^ uy ^ ut, car = (ux & uy) | (ut & (ux ^ uy));
+                    const uint64_t h1 = o1 & sum;
+                    o1 ^= sum;
+                    const uint64_t h2 = (o2 & car) | (h1 & (o2 ^ car));
+                    o2 ^= car ^ h1;
+                    const uint64_t h4 = o4 & h2;
+                    o4 ^= h2;
+                    o8 ^= h4;  // at most 5 * 3 = 15 per position: no carry out of o8
+                }
+            }
+            // c += (o8 o4 o2 o1): ripple over the low planes (a thread counts at
+            // most 3 * kEnergyRun < 2^10 per position)
+            uint64_t carry = 0;
+            const uint64_t in[4] = {o1, o2, o4, o8};
+#pragma unroll
+            for (int p = 0; p < 10; ++p) {
+                const uint64_t b = p < 4 ? in[p] : 0ull;
+                const uint64_t sp = c[p] ^ b ^ carry;
+                carry = (c[p] & b) | (carry & (c[p] ^ b));
+                c[p] = sp;
+            }
+        }
+    }
+    // warp sum of the bitsliced counters (at most 32 * 3 * kEnergyRun < 2^16)
+    for (int o = 16; o > 0; o >>= 1) {
+        uint64_t other[kEnergyPlanes];
+#pragma unroll
+        for (int p = 0; p < kEnergyPlanes; ++p) other[p] = __shfl_down_sync(0xffffffffu, c[p], o);
+        vadd_counter(c, other);
+    }
+    // lane l turns sample bits l and l + 32 of lane 0's counter into integers
+    {
+        const int lane = threadIdx.x & 31;
+        int v0 = 0, v1 = 0;
+#pragma unroll
+        for (int p = 0; p < kEnergyPlanes; ++p) {
+            const uint64_t cp = __shfl_sync(0xffffffffu, c[p], 0);
+            v0 |= (int)((cp >> lane) & 1ull) << p;
+            v1 |= (int)((cp >> (lane + 32)) & 1ull) << p;
+        }
+        if (v0) atomicAdd(&cnt[lane], v0);
+        if (v1) atomicAdd(&cnt[lane + 32], v1);
     }
     __syncthreads();
-    if (threadIdx.x < 64) atomicAdd(&g.U[(size_t)s * 64 + threadIdx.x], cnt[threadIdx.x]);
+    for (int b = threadIdx.x; b < 64; b += blockDim.x)
+        if (cnt[b]) atomicAdd(&g.U[(size_t)s * 64 + b], cnt[b]);
 }
 
 cudaError_t launch_energy(const Group &g, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g.U, 0, sizeof(int32_t) * (size_t)g.nslots * 64, st);
     if (e != cudaSuccess) return e;
-    // <= 3 * 64 * 256 bonds per thread keeps every count below 2^16
-    const int spb = kEnergyThreads * 64;
-    dim3 grid((g.N + spb - 1) / spb, g.nslots);
+    const int L2 = g.L * g.L;
+    const int threads = L2 >= 256 ? 256 : ((L2 + 31) / 32) * 32;
+    dim3 grid((L2 + threads - 1) / threads, g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
     count_launches(1);
-    k_energy<<<grid, kEnergyThreads, 0, st>>>(g, spb);
+    k_energy<<<grid, threads, 0, st>>>(g);
     return cudaGetLastError();
 }
 
