@@ -173,6 +173,35 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
+/* Sweeps without any device allocation.  (This entry point has no
+ * counterpart in the paper: it is a service for callers of this library.)
+ *
+ * Some callers cannot allocate device memory themselves: a plugin or service
+ * whose GPU memory is owned by the host application's allocator or held to a
+ * fixed budget, or code that must avoid the device-wide synchronisation that
+ * cudaMalloc and cudaFree can cause.  Such a caller passes its own buffers --
+ * d_spins [slots][L_tau][L][L] words (read and written), d_Jx and d_Jy
+ * [words][L][L] coupling words as described above -- and this function runs
+ * n_sweeps full sweeps of the fused wavefront kernel on them, exactly as
+ * qsg_sweep does for a context (the same bits for the same seed, group_id and
+ * sweep counter first_sweep).  k_ladder (host) holds the n_k values of the
+ * ladder; the acceptance table is built from it on each call.
+ *
+ * The kernel's scratch (its chunk-boundary arrival counters and the
+ * acceptance table) lives in two fixed arrays in device memory that every GPU
+ * loading this library holds until the process exits: at most 2^20 counters
+ * (slots x tau chunks) and 128 ladder positions; larger shapes are rejected
+ * with QSG_ERR_ARG, shapes with L_tau not a multiple of 16 with QSG_ERR_SHAPE.
+ * The first call on a device looks the arrays up and clears the counters, so
+ * it should come before any stream capture on that device.  Every call shares
+ * the same arrays: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  The call copies the
+ * table to the device and waits for that copy on cuda_stream; the sweeps are
+ * enqueued on cuda_stream without waiting.  Nothing is allocated. */
+qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t *d_Jx, const uint64_t *d_Jy,
+                                    const qsg_shape *shape, int32_t group_id, const double *k_ladder, uint64_t seed,
+                                    uint32_t first_sweep, int32_t n_sweeps, void *cuda_stream);
+
 /* Number of kernels this library has launched in this process (all contexts);
  * a diagnostic for benchmarks and for checking that the GPU path ran. */
 uint64_t qsg_kernel_launches(void);

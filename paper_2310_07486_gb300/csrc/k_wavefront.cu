@@ -418,4 +418,127 @@ cudaError_t launch_sweep_wavefront(const Group &g, uint32_t sweep, uint64_t seed
     return launch_wf_algo<1>(g, C, sweep, seed, arrivals, st);
 }
 
+// ---------------------------------------------------------------------------
+// Sweep entry point that allocates nothing.
+//
+// Its scratch -- the boundary arrival counters of the wavefront kernel and the
+// acceptance table -- lives in the two file-scope device arrays below, so a
+// caller that cannot allocate device memory only has to pass its own spin and
+// coupling buffers.  Every GPU that loads the library keeps these arrays until
+// the process exits.
+// ---------------------------------------------------------------------------
 }  // namespace qsg
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "qsg.h"
+
+namespace qsg {
+namespace {
+
+constexpr int kStaticArrivals = 1 << 20;  // counters: slots x chunks per call (4 MiB)
+constexpr int kStaticMaxK = 128;          // ladder positions (16 thresholds each)
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned g_static_arrivals[kStaticArrivals];
+__device__ __align__(256) uint32_t g_static_thr[kStaticMaxK * 16];
+
+std::mutex g_static_mutex;
+void *g_static_arrivals_ptr[kMaxDevices];
+void *g_static_thr_ptr[kMaxDevices];
+
+// Device addresses of the two arrays on the current device (looked up and the
+// counters cleared on the first call on that device).
+cudaError_t static_scratch(void **arrivals, void **thr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_arrivals_ptr[dev]) {
+        void *a = nullptr, *t = nullptr;
+        e = cudaGetSymbolAddress(&a, g_static_arrivals);
+        if (e != cudaSuccess) return e;
+        e = cudaGetSymbolAddress(&t, g_static_thr);
+        if (e != cudaSuccess) return e;
+        e = cudaMemset(a, 0, sizeof(unsigned) * kStaticArrivals);
+        if (e != cudaSuccess) return e;
+        g_static_arrivals_ptr[dev] = a;
+        g_static_thr_ptr[dev] = t;
+    }
+    *arrivals = g_static_arrivals_ptr[dev];
+    *thr = g_static_thr_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace qsg
+
+extern "C" qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t *d_Jx, const uint64_t *d_Jy,
+                                               const qsg_shape *shape, int32_t group_id, const double *k_ladder,
+                                               uint64_t seed, uint32_t first_sweep, int32_t n_sweeps,
+                                               void *cuda_stream) {
+    using namespace qsg;
+    if (!d_spins || !d_Jx || !d_Jy || !shape || !k_ladder || n_sweeps < 0 || group_id < 0 || group_id > 255)
+        return QSG_ERR_ARG;
+    const qsg_shape &sh = *shape;
+    if (sh.L < 2 || sh.L > 32 || (sh.L & 1) || sh.Ltau < 16 || sh.Ltau > 65536 || sh.n_samples < 1 ||
+        sh.n_replicas < 1 || sh.n_k < 1 || (sh.algo != QSG_METROPOLIS && sh.algo != QSG_HEATBATH) ||
+        (sh.boundary != QSG_PBC && sh.boundary != QSG_APBC) || sh.reserved != 0)
+        return QSG_ERR_SHAPE;
+    if ((uint64_t)first_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
+    Group g;
+    memset(&g, 0, sizeof(g));
+    g.L = sh.L;
+    g.Ltau = sh.Ltau;
+    g.W = (sh.n_samples + 63) / 64;
+    g.R = sh.n_replicas;
+    g.K = sh.n_k;
+    g.algo = sh.algo;
+    g.boundary = sh.boundary;
+    g.gid = group_id;
+    g.N = sh.L * sh.L * sh.Ltau;
+    g.nslots = g.W * g.R * g.K;
+    g.nlag = sh.Ltau / 2 + 1;
+    g.n_samples = sh.n_samples;
+    g.nwx = (sh.L * sh.L + 63) / 64;
+    const int C = wavefront_chunk(g, 0);
+    if (C == 0) return QSG_ERR_SHAPE;  // L_tau must be a multiple of 16
+    // the limits of the static scratch
+    if (g.K > kStaticMaxK || (long long)g.nslots * (g.Ltau / C) > kStaticArrivals) return QSG_ERR_ARG;
+    // acceptance table (same definitions as qsg_init_samples), on the stack
+    uint32_t table[kStaticMaxK * 16];
+    for (int j = 0; j < g.K; ++j) {
+        const double k = k_ladder[j];
+        if (!(k > 0.0) || !(k < 3.0) || (j > 0 && !(k > k_ladder[j - 1]))) return QSG_ERR_ARG;
+        for (int n = 0; n < 16; ++n) table[16 * j + n] = 0u;
+        for (int c = 0; c < 3; ++c)
+            table[16 * j + c] = (uint32_t)std::floor(std::exp(-(2.0 * k * (double)(2 * (c + 1)))) * 4294967296.0);
+        for (int n = 0; n < 7; ++n) {
+            const double p = 1.0 / (1.0 + std::exp(-(2.0 * k * (double)(6 - 2 * n))));
+            double t = std::floor(p * 4294967296.0);
+            if (t > 4294967295.0) t = 4294967295.0;
+            table[16 * j + 8 + n] = (uint32_t)t;
+        }
+    }
+    void *arr = nullptr, *thr = nullptr;
+    if (static_scratch(&arr, &thr) != cudaSuccess) return QSG_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    // the table lives on this function's stack: copy it and wait for the copy
+    if (cudaMemcpyAsync(thr, table, sizeof(uint32_t) * 16 * (size_t)g.K, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return QSG_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return QSG_ERR_CUDA;
+    // counters start at zero (each sweep leaves them at zero; cleared anyway)
+    if (cudaMemsetAsync(arr, 0, sizeof(unsigned) * (size_t)g.nslots * (g.Ltau / C), st) != cudaSuccess)
+        return QSG_ERR_CUDA;
+    g.S = d_spins;
+    g.Jx = const_cast<uint64_t *>(d_Jx);
+    g.Jy = const_cast<uint64_t *>(d_Jy);
+    g.thr = (uint32_t *)thr;
+    for (int it = 0; it < n_sweeps; ++it)
+        if (launch_sweep_wavefront(g, first_sweep + (uint32_t)it, seed, (unsigned *)arr, C, st) != cudaSuccess)
+            return QSG_ERR_CUDA;
+    return QSG_OK;
+}

@@ -82,6 +82,8 @@ def load_library(path: str | None = None):
     lib.qsg_get_counters.argtypes = [vp, vp, vp, vp]
     lib.qsg_set_counters.restype = i32
     lib.qsg_set_counters.argtypes = [vp, u32, u32, ctypes.c_int64]
+    lib.qsg_sweep_static_scratch.restype = i32
+    lib.qsg_sweep_static_scratch.argtypes = [vp, vp, vp, vp, i32, vp, u64, u32, i32, vp]
     lib.qsg_set_option.restype = i32
     lib.qsg_set_option.argtypes = [vp, i32, ctypes.c_int64]
     lib.qsg_kernel_launches.restype = ctypes.c_uint64
@@ -98,7 +100,23 @@ def exported_symbols():
     return ["qsg_workspace_bytes", "qsg_create", "qsg_destroy", "qsg_set_stream", "qsg_init_samples",
             "qsg_set_couplings", "qsg_sweep", "qsg_tempering_swap", "qsg_measure_correlators",
             "qsg_read_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
-            "qsg_get_counters", "qsg_set_counters", "qsg_set_option", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
+            "qsg_get_counters", "qsg_set_counters", "qsg_set_option", "qsg_sweep_static_scratch", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
+
+
+def qsg_sweep_static_scratch(spins, Jx, Jy, shape: "Shape", group_id, ladder, seed, first_sweep, n_sweeps,
+                             stream=None):
+    """Sweeps on caller-owned device buffers (torch tensors of 64-bit words)
+    without any device allocation by the library."""
+    import torch
+    lad = np.ascontiguousarray(np.asarray(ladder, dtype=np.float64))
+    sh = shape.c()
+    st = stream if stream is not None else torch.cuda.current_stream()
+    status = load_library().qsg_sweep_static_scratch(
+        ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(Jx.data_ptr()), ctypes.c_void_p(Jy.data_ptr()),
+        ctypes.byref(sh), int(group_id), _ptr(lad), int(seed) & ((1 << 64) - 1), int(first_sweep), int(n_sweeps),
+        ctypes.c_void_p(st.cuda_stream))
+    if status != 0:
+        raise QSGError(status, "qsg_sweep_static_scratch")
 
 
 def qsg_kernel_launches() -> int:
