@@ -169,8 +169,14 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *   QSG_OPT_CORR_KERNEL   0 = tensor cores (Gram tiles by tcgen05.mma in FP8,
  *                         exact for +-1 spins), 1 = XOR/popcount on the
  *                         integer pipes
+ *   QSG_OPT_PERSISTENT    0 = automatic (on when the context has several
+ *                         groups), 1 = off (one launch per group and sweep),
+ *                         2 = on: one persistent launch per sweep serves every
+ *                         group from a work queue, largest groups first (needs
+ *                         one algorithm, L <= 24, every L_tau % 16 == 0)
  * Results do not depend on the options: every kernel produces the same bits. */
-enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4 };
+enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
+       QSG_OPT_PERSISTENT = 5 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

@@ -1,5 +1,6 @@
 // api.cu -- host side of the C ABI declared in include/qsg.h: validation,
 // workspace carving, acceptance tables, and the ordering of kernel launches.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -58,8 +59,15 @@ int a_cap(const Group &g) {
     return (int)(need < kMaxA ? need : kMaxA);
 }
 
+struct PlanBuffers {
+    Group *groups = nullptr;
+    int *order = nullptr, *prefix = nullptr, *chunk = nullptr;
+    unsigned *queue = nullptr;
+};
+
 // Walk the workspace: when base is null only the size is computed.
-size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, size_t *scratch_words) {
+size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, size_t *scratch_words,
+             PlanBuffers *pb = nullptr) {
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         char *p = base ? base + off : nullptr;
@@ -99,6 +107,20 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
     }
     *scratch = (uint64_t *)take(sizeof(uint64_t) * sw);
     *scratch_words = sw;
+    // persistent-launch plan: group table, order, unit prefix sums, chunks, queue
+    const size_t ng = gs.size();
+    Group *pg = (Group *)take(sizeof(Group) * ng);
+    int *po = (int *)take(sizeof(int) * ng);
+    int *pp = (int *)take(sizeof(int) * (ng + 1));
+    int *pc = (int *)take(sizeof(int) * ng);
+    unsigned *pq = (unsigned *)take(sizeof(unsigned) * 2);
+    if (pb) {
+        pb->groups = pg;
+        pb->order = po;
+        pb->prefix = pp;
+        pb->chunk = pc;
+        pb->queue = pq;
+    }
     return off;
 }
 
@@ -138,6 +160,10 @@ struct qsg_ctx {
     int sweep_kernel = 0;  // QSG_OPT_SWEEP_KERNEL
     int chunk = 0;         // QSG_OPT_CHUNK
     int corr_tensor = 1;   // QSG_OPT_CORR_KERNEL: 1 tensor cores, 0 integer pipes
+    int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 on
+    PlanBuffers pb;
+    PersistentPlan plan{};
+    bool plan_ok = false;
     std::string last_cuda;
 };
 
@@ -158,6 +184,36 @@ static qsg_status check_device_flag(qsg_ctx *c) {
     QSG_CUDA(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     QSG_CUDA(c, cudaStreamSynchronize(c->stream));
     return h == DEVERR_NONE ? QSG_OK : QSG_ERR_TIMEOUT;
+}
+
+// Build the persistent-launch plan (all groups with the same algorithm, L <= 24,
+// L_tau a multiple of 16) and copy it to the workspace.
+static qsg_status upload_plan(qsg_ctx *c) {
+    c->plan_ok = false;
+    const int ng = (int)c->groups.size();
+    for (const Group &g : c->groups)
+        if (g.algo != c->groups[0].algo || g.L > 24 || wavefront_chunk(g, c->chunk) == 0) return QSG_OK;
+    std::vector<int> order(ng), prefix(ng + 1, 0), chunk(ng);
+    for (int i = 0; i < ng; ++i) {
+        order[i] = i;
+        chunk[i] = wavefront_chunk(c->groups[i], c->chunk);
+    }
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        return (double)c->groups[x].nslots * c->groups[x].N > (double)c->groups[y].nslots * c->groups[y].N;
+    });
+    for (int i = 0; i < ng; ++i) {
+        const Group &g = c->groups[order[i]];
+        prefix[i + 1] = prefix[i] + g.nslots * (g.Ltau / chunk[order[i]]);
+    }
+    QSG_CUDA(c, cudaMemcpyAsync(c->pb.groups, c->groups.data(), sizeof(Group) * ng, cudaMemcpyHostToDevice, c->stream));
+    QSG_CUDA(c, cudaMemcpyAsync(c->pb.order, order.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream));
+    QSG_CUDA(c, cudaMemcpyAsync(c->pb.prefix, prefix.data(), sizeof(int) * (ng + 1), cudaMemcpyHostToDevice, c->stream));
+    QSG_CUDA(c, cudaMemcpyAsync(c->pb.chunk, chunk.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, c->stream));
+    QSG_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->plan = PersistentPlan{c->pb.groups, c->pb.order, c->pb.prefix, c->pb.chunk, c->pb.queue, ng, prefix[ng],
+                             c->groups[0].algo};
+    c->plan_ok = true;
+    return QSG_OK;
 }
 
 extern "C" {
@@ -189,19 +245,20 @@ qsg_status qsg_create(qsg_ctx **out, const qsg_shape *shapes, int32_t n_groups, 
     for (int i = 0; i < n_groups; ++i) c->groups.push_back(describe(shapes[i], i));
     c->ws = (char *)d_workspace;
     c->ws_bytes = workspace_bytes;
-    carve(c->groups, c->ws, &c->d_err, &c->scratch, &c->scratch_words);
+    carve(c->groups, c->ws, &c->d_err, &c->scratch, &c->scratch_words, &c->pb);
     c->stream = (cudaStream_t)cuda_stream;
     cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int) * 4, c->stream);
     for (const Group &g : c->groups)
         if (e == cudaSuccess)
             e = cudaMemsetAsync(g.arrivals, 0, sizeof(unsigned) * (size_t)g.nslots * (g.Ltau / 4 > 0 ? g.Ltau / 4 : 1),
                                 c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->pb.queue, 0, sizeof(unsigned) * 2, c->stream);
     if (e != cudaSuccess) {
         delete c;
         return QSG_ERR_CUDA;
     }
     *out = c;
-    return QSG_OK;
+    return upload_plan(c);
 }
 
 void qsg_destroy(qsg_ctx *ctx) { delete ctx; }
@@ -306,11 +363,17 @@ qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
     if (!ctx || n_sweeps < 0) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
-    for (int it = 0; it < n_sweeps; ++it) {
+    const bool persistent = ctx->plan_ok && ctx->sweep_kernel != 1 &&
+                            (ctx->persistent == 2 || (ctx->persistent == 0 && ctx->groups.size() > 1));
+    for (int it = 0; it < n_sweeps && persistent; ++it) {
+        QSG_CUDA(ctx, launch_sweep_persistent(ctx->plan, nullptr, ctx->sweeps, ctx->seed, ctx->stream));
+        ctx->sweeps++;
+    }
+    for (int it = 0; it < n_sweeps && !persistent; ++it) {
         for (const Group &g : ctx->groups) {
             const int C = ctx->sweep_kernel == 1 ? 0 : wavefront_chunk(g, ctx->chunk);
             if (C > 0)
-                QSG_CUDA(ctx, launch_sweep_wavefront(g, ctx->sweeps, ctx->seed, g.arrivals, C, ctx->stream));
+                QSG_CUDA(ctx, launch_sweep_wavefront(g, nullptr, ctx->sweeps, ctx->seed, g.arrivals, C, ctx->stream));
             else
                 QSG_CUDA(ctx, launch_sweep_reference(g, ctx->sweeps, ctx->seed, ctx->stream));
         }
@@ -466,6 +529,12 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         g_wavefront_variant = (int)value;
         return QSG_OK;
     }
+    if (option == QSG_OPT_PERSISTENT) {
+        if (value < 0 || value > 2) return QSG_ERR_ARG;
+        if (value == 2 && !ctx->plan_ok) return QSG_ERR_ARG;
+        ctx->persistent = (int)value;
+        return QSG_OK;
+    }
     if (option == QSG_OPT_CORR_KERNEL) {
         if (value < 0 || value > 1) return QSG_ERR_ARG;
         ctx->corr_tensor = value == 0 ? 1 : 0;
@@ -477,7 +546,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
             for (const Group &g : ctx->groups)
                 if (wavefront_chunk(g, (int)value) == 0) return QSG_ERR_ARG;
         ctx->chunk = (int)value;
-        return QSG_OK;
+        return upload_plan(ctx);
     }
     return QSG_ERR_ARG;
 }

@@ -81,6 +81,14 @@ __global__ void k_half_sweep_ref(Group g, int colour, uint32_t sweep, uint32_t k
     }
 }
 
+__global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
+
+cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st) {
+    count_launches(1);
+    k_set_word<<<1, 1, 0, st>>>(p, value);
+    return cudaGetLastError();
+}
+
 static int grid_for(long long work, int block) {
     long long g = (work + block - 1) / block;
     if (g > 152 * 32) g = 152 * 32;

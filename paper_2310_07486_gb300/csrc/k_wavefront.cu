@@ -182,26 +182,22 @@ __device__ __forceinline__ void boundary_update(const Group &g, const Thr &t, ui
 // program.  A super step (q = a + 2m) therefore runs
 //     colour 0 of planes q, q+1  |barrier|  colour 1 of planes q-1, q
 // with one barrier per two planes.
-template <int ALGO, int SLOT, int NREG>
-__global__ void __launch_bounds__(512) __maxnreg__(NREG)
-    k_sweep_wavefront(const Group g, const int C, const int nch, const int P, const uint32_t sweep, const uint32_t k0,
-                      const uint32_t k1, unsigned *__restrict__ arrivals) {
-    extern __shared__ __align__(16) uint64_t smem[];
-    __shared__ int do_boundary[32];
+// One work unit (slot s, chunk ch of C planes) run by the threads that share
+// `ring` (kRing * SLOT + 2 L^2 words of shared memory); threads with
+// active == false only take part in the barriers.  do_boundary is one int of
+// shared memory for this unit.
+template <int ALGO, int SLOT>
+__device__ __forceinline__ void wavefront_unit(const Group &g, const int C, const int nch, const int s, const int ch,
+                                               const bool active, const int c, uint64_t *ring, int *do_boundary,
+                                               const uint32_t sweep, const uint32_t k0, const uint32_t k1,
+                                               unsigned *__restrict__ arrivals) {
     const int L = g.L, L2 = L * L, Lt = g.Ltau, half = L / 2;
-    const int tpu = L2 / 2;
-    const int u = threadIdx.x / tpu, c = threadIdx.x - u * tpu;
-    const int unit = blockIdx.x * P + u;
-    const bool active = unit < g.nslots * nch;
-    const int s = active ? unit / nch : 0;
-    const int ch = active ? unit - s * nch : 0;
     const int a = ch * C, b = a + C;
     const int w = s / (g.R * g.K), j = s % g.K;
-    uint64_t *ring = smem + (size_t)u * (kRing * SLOT + 2 * L2);
     uint64_t *sJx = ring + kRing * SLOT, *sJy = sJx + L2;
     uint64_t *Sg = g.S + (size_t)s * g.N;
     const Thr t = make_thr(L, c);
-    {
+    if (active) {
         // couplings of word-group w, stored class-split like the spin planes
         const uint64_t *gJx = g.Jx + (size_t)w * L2, *gJy = g.Jy + (size_t)w * L2;
         sJx[t.dA] = gJx[2 * c];
@@ -332,16 +328,78 @@ __global__ void __launch_bounds__(512) __maxnreg__(NREG)
             if (atomicAdd(&arrivals[s * nch + chn], 1u) == 1u) flags |= 2;
             __threadfence();
         }
-        do_boundary[u] = flags;
+        *do_boundary = flags;
     }
     __syncthreads();
-    const int flags = do_boundary[u];
+    const int flags = *do_boundary;
     if (active && flags) {
         if (flags & 1) boundary_update<ALGO>(g, t, Sg, sJx, sJy, a, T, sweep, (uint32_t)s, k0, k1);
         if (flags & 2) boundary_update<ALGO>(g, t, Sg, sJx, sJy, b == Lt ? 0 : b, T, sweep, (uint32_t)s, k0, k1);
         if (c == 0) {
             if (flags & 1) arrivals[s * nch + ch] = 0u;
             if (flags & 2) arrivals[s * nch + chn] = 0u;
+        }
+    }
+}
+
+// One launch per sweep of one group: P units per block (blocks of P * L^2 / 2 threads).
+template <int ALGO, int SLOT, int NREG>
+__global__ void __launch_bounds__(512) __maxnreg__(NREG)
+    k_sweep_wavefront(const Group g, const int C, const int nch, const int P, const uint32_t *sweep_base,
+                      const uint32_t sweep_off, const uint32_t k0, const uint32_t k1, unsigned *__restrict__ arrivals) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ int do_boundary[32];
+    // absolute sweep index (keys Philox): a device counter plus an offset, so
+    // that a captured graph of several sweeps can be replayed at any point
+    const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
+    const int L2 = g.L * g.L, tpu = L2 / 2;
+    const int u = threadIdx.x / tpu, c = threadIdx.x - u * tpu;
+    const int unit = blockIdx.x * P + u;
+    const bool active = unit < g.nslots * nch;
+    const int s = active ? unit / nch : 0;
+    const int ch = active ? unit - s * nch : 0;
+    wavefront_unit<ALGO, SLOT>(g, C, nch, s, ch, active, c, smem + (size_t)u * (kRing * SLOT + 2 * L2),
+                               &do_boundary[u], sweep, k0, k1, arrivals);
+}
+
+// One launch per sweep of several groups of different sizes (same algorithm):
+// a persistent grid pulls units from a queue ordered largest group first;
+// every block has 288 threads and SLOT >= the largest L^2, threads beyond a
+// unit's L^2 / 2 idle.  queue[0] hands out units, queue[1] counts the blocks
+// that have finished; the last one resets both for the next launch.
+template <int ALGO, int SLOT, int NREG>
+__global__ void __launch_bounds__(288) __maxnreg__(NREG)
+    k_sweep_persistent(const Group *__restrict__ groups, const int *__restrict__ order,
+                       const int *__restrict__ prefix, const int *__restrict__ chunk, const int ngroups,
+                       unsigned *__restrict__ queue, const uint32_t *sweep_base, const uint32_t sweep_off,
+                       const uint32_t k0, const uint32_t k1) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ int do_boundary;
+    __shared__ int s_unit;
+    const uint32_t sweep = (sweep_base ? *sweep_base : 0u) + sweep_off;
+    const int total = prefix[ngroups];
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = (int)atomicAdd(&queue[0], 1u);
+        __syncthreads();
+        const int unit = s_unit;
+        __syncthreads();
+        if (unit >= total) break;
+        int k = 0;
+        while (k + 1 < ngroups && unit >= prefix[k + 1]) ++k;
+        const Group g = groups[order[k]];
+        const int C = chunk[order[k]], nch = g.Ltau / C;
+        const int lu = unit - prefix[k];
+        const int s = lu / nch, ch = lu - s * nch;
+        const bool active = (int)threadIdx.x < g.L * g.L / 2;
+        wavefront_unit<ALGO, SLOT>(g, C, nch, s, ch, active, active ? (int)threadIdx.x : 0, smem, &do_boundary, sweep,
+                                   k0, k1, g.arrivals);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&queue[1], 1u) == gridDim.x - 1) {
+            queue[0] = 0u;
+            queue[1] = 0u;
         }
     }
 }
@@ -367,7 +425,8 @@ int wavefront_units_per_block(const Group &g) {
 }
 
 template <int ALGO, int SLOT, int NREG>
-static cudaError_t launch_wf(const Group &g, int C, uint32_t sweep, uint64_t seed, unsigned *arrivals, cudaStream_t st) {
+static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
+                             unsigned *arrivals, cudaStream_t st) {
     const int nch = g.Ltau / C;
     const int P = wavefront_units_per_block(g);
     const int units = g.nslots * nch;
@@ -381,7 +440,7 @@ static cudaError_t launch_wf(const Group &g, int C, uint32_t sweep, uint64_t see
                                  100);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_sweep_wavefront<ALGO, SLOT, NREG><<<blocks, threads, sm, st>>>(g, C, nch, P, sweep, (uint32_t)seed,
+    k_sweep_wavefront<ALGO, SLOT, NREG><<<blocks, threads, sm, st>>>(g, C, nch, P, sweep_base, sweep, (uint32_t)seed,
                                                                      (uint32_t)(seed >> 32), arrivals);
     return cudaGetLastError();
 }
@@ -390,32 +449,70 @@ static cudaError_t launch_wf(const Group &g, int C, uint32_t sweep, uint64_t see
 // thread at 96 registers (two blocks of <= 288 threads per SM), variant 1 at
 // 72 (three blocks); blocks of more than 288 threads get 64.
 template <int ALGO, int SLOT>
-static cudaError_t launch_wf_slot(const Group &g, int C, uint32_t sweep, uint64_t seed, unsigned *arrivals,
-                                  cudaStream_t st) {
+static cudaError_t launch_wf_slot(const Group &g, int C, const uint32_t *sb, uint32_t sweep, uint64_t seed,
+                                  unsigned *arrivals, cudaStream_t st) {
     const int threads = wavefront_units_per_block(g) * (g.L * g.L / 2);
-    if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, sweep, seed, arrivals, st);
-    if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, sweep, seed, arrivals, st);
-    return launch_wf<ALGO, SLOT, 96>(g, C, sweep, seed, arrivals, st);
+    if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, sb, sweep, seed, arrivals, st);
+    if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, sb, sweep, seed, arrivals, st);
+    return launch_wf<ALGO, SLOT, 96>(g, C, sb, sweep, seed, arrivals, st);
 }
 
 // Ring planes are padded to the next of a few sizes (exact for L = 8, 12, 16,
 // 20, 24, 32).
 template <int ALGO>
-static cudaError_t launch_wf_algo(const Group &g, int C, uint32_t sweep, uint64_t seed, unsigned *arrivals,
-                                  cudaStream_t st) {
+static cudaError_t launch_wf_algo(const Group &g, int C, const uint32_t *sb, uint32_t sweep, uint64_t seed,
+                                  unsigned *arrivals, cudaStream_t st) {
     const int L2 = g.L * g.L;
-    if (L2 <= 64) return launch_wf_slot<ALGO, 64>(g, C, sweep, seed, arrivals, st);
-    if (L2 <= 144) return launch_wf_slot<ALGO, 144>(g, C, sweep, seed, arrivals, st);
-    if (L2 <= 256) return launch_wf_slot<ALGO, 256>(g, C, sweep, seed, arrivals, st);
-    if (L2 <= 400) return launch_wf_slot<ALGO, 400>(g, C, sweep, seed, arrivals, st);
-    if (L2 <= 576) return launch_wf_slot<ALGO, 576>(g, C, sweep, seed, arrivals, st);
-    return launch_wf_slot<ALGO, 1024>(g, C, sweep, seed, arrivals, st);
+    if (L2 <= 64) return launch_wf_slot<ALGO, 64>(g, C, sb, sweep, seed, arrivals, st);
+    if (L2 <= 144) return launch_wf_slot<ALGO, 144>(g, C, sb, sweep, seed, arrivals, st);
+    if (L2 <= 256) return launch_wf_slot<ALGO, 256>(g, C, sb, sweep, seed, arrivals, st);
+    if (L2 <= 400) return launch_wf_slot<ALGO, 400>(g, C, sb, sweep, seed, arrivals, st);
+    if (L2 <= 576) return launch_wf_slot<ALGO, 576>(g, C, sb, sweep, seed, arrivals, st);
+    return launch_wf_slot<ALGO, 1024>(g, C, sb, sweep, seed, arrivals, st);
 }
 
-cudaError_t launch_sweep_wavefront(const Group &g, uint32_t sweep, uint64_t seed, unsigned *arrivals, int C,
-                                   cudaStream_t st) {
-    if (g.algo == 0) return launch_wf_algo<0>(g, C, sweep, seed, arrivals, st);
-    return launch_wf_algo<1>(g, C, sweep, seed, arrivals, st);
+cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
+                                   unsigned *arrivals, int C, cudaStream_t st) {
+    if (g.algo == 0) return launch_wf_algo<0>(g, C, sweep_base, sweep, seed, arrivals, st);
+    return launch_wf_algo<1>(g, C, sweep_base, sweep, seed, arrivals, st);
+}
+
+template <int ALGO>
+static cudaError_t launch_persistent_algo(const PersistentPlan &pl, const uint32_t *sweep_base, uint32_t sweep,
+                                          uint64_t seed, cudaStream_t st) {
+    constexpr int SLOT = 576, NREG = 96, THREADS = 288;
+    const size_t sm = (size_t)(kRing * SLOT + 2 * SLOT) * sizeof(uint64_t);
+    static int blocks_per_sm[2] = {0, 0};
+    cudaError_t e;
+    if (!blocks_per_sm[ALGO]) {
+        e = cudaFuncSetAttribute(k_sweep_persistent<ALGO, SLOT, NREG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sm);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_sweep_persistent<ALGO, SLOT, NREG>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int n = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_sweep_persistent<ALGO, SLOT, NREG>, THREADS, sm);
+        if (e != cudaSuccess) return e;
+        blocks_per_sm[ALGO] = n > 0 ? n : 1;
+    }
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int blocks = sms * blocks_per_sm[ALGO];
+    if (blocks > pl.total_units) blocks = pl.total_units;
+    count_launches(1);
+    k_sweep_persistent<ALGO, SLOT, NREG><<<blocks, THREADS, sm, st>>>(pl.groups, pl.order, pl.prefix, pl.chunk,
+                                                                      pl.ngroups, pl.queue, sweep_base, sweep,
+                                                                      (uint32_t)seed, (uint32_t)(seed >> 32));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_persistent(const PersistentPlan &pl, const uint32_t *sweep_base, uint32_t sweep,
+                                    uint64_t seed, cudaStream_t st) {
+    if (pl.algo == 0) return launch_persistent_algo<0>(pl, sweep_base, sweep, seed, st);
+    return launch_persistent_algo<1>(pl, sweep_base, sweep, seed, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -538,7 +635,7 @@ extern "C" qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t
     g.Jy = const_cast<uint64_t *>(d_Jy);
     g.thr = (uint32_t *)thr;
     for (int it = 0; it < n_sweeps; ++it)
-        if (launch_sweep_wavefront(g, first_sweep + (uint32_t)it, seed, (unsigned *)arr, C, st) != cudaSuccess)
+        if (launch_sweep_wavefront(g, nullptr, first_sweep + (uint32_t)it, seed, (unsigned *)arr, C, st) != cudaSuccess)
             return QSG_ERR_CUDA;
     return QSG_OK;
 }

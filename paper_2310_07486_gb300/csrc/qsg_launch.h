@@ -24,8 +24,24 @@ cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed
 // use this kernel), arrivals = nslots * (L_tau / 4) zeroed counters.
 int wavefront_chunk(const Group &g, int requested);
 extern int g_wavefront_variant;  // 0: register cap for 3 blocks/SM when blocks <= 288 threads; 1: 2 blocks/SM
-cudaError_t launch_sweep_wavefront(const Group &g, uint32_t sweep, uint64_t seed, unsigned *arrivals, int C,
-                                   cudaStream_t st);
+// The sweep index is *sweep_base + sweep (sweep_base may be null), so that a
+// captured CUDA graph of several sweeps can be replayed later.
+cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
+                                   unsigned *arrivals, int C, cudaStream_t st);
+cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st);
+
+// All groups of a context in one persistent launch per sweep (same algorithm,
+// L <= 24, L_tau % 16 == 0).  Device arrays: the Group structs, the group
+// order (largest first), the prefix sums of work units in that order, the
+// chunk length of every group, and two queue counters (zero between launches).
+struct PersistentPlan {
+    const Group *groups;
+    const int *order, *prefix, *chunk;
+    unsigned *queue;
+    int ngroups, total_units, algo;
+};
+cudaError_t launch_sweep_persistent(const PersistentPlan &plan, const uint32_t *sweep_base, uint32_t sweep,
+                                    uint64_t seed, cudaStream_t st);
 
 // Unsatisfied-bond counts U[slot][bit] of the current configurations.
 cudaError_t launch_energy(const Group &g, cudaStream_t st);

@@ -282,3 +282,46 @@ def test_correlator_kernels_match_oracle(L, Ltau, boundary):
     orc.measure()
     orc.measure()
     _check_corr(ctx.qsg_read_correlators(raw=True), orc.read())
+
+
+@pytest.mark.parametrize("algo", [Q.METROPOLIS, Q.HEATBATH])
+def test_persistent_ragged_launch_matches_oracle(algo):
+    """Groups of different (L, L_tau) in one persistent launch per sweep: every
+    group's spins equal the oracle's and the per-group launches'."""
+    shapes = [Q.Shape(8, 32, 70, 2, 3, algo, Q.PBC), Q.Shape(12, 64, 5, 1, 2, algo, Q.APBC),
+              Q.Shape(6, 16, 64, 2, 2, algo, Q.PBC), Q.Shape(16, 48, 3, 1, 1, algo, Q.PBC)]
+    lads = [np.array([0.2, 0.3, 0.4]), np.array([0.25, 0.33]), np.array([0.27, 0.28]), np.array([0.3])]
+    results = []
+    for mode in (2, 1):  # persistent on, off
+        ctx = Q.Context(shapes)
+        ctx.qsg_init_samples(23, lads)
+        ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
+        for _ in range(3):
+            ctx.qsg_sweep(2)
+            ctx.qsg_tempering_swap()
+        results.append([ctx.qsg_get_spins(gi) for gi in range(len(shapes))])
+    for a, b in zip(*results):
+        assert np.array_equal(a, b)
+    for gid, (s, l) in enumerate(zip(shapes, lads)):
+        o = oracle.OracleGroup(s.L, s.Ltau, s.n_samples, s.n_replicas, s.n_k, algo=s.algo, boundary=s.boundary,
+                               group_id=gid)
+        o.init(23, l)
+        for _ in range(3):
+            o.sweep(2)
+            o.swap()
+        assert np.array_equal(Q.unpack_spins(results[0][gid], s), o.spins()), gid
+
+
+def test_ragged_workload_persistent_equals_per_group():
+    w = workloads.ragged()
+    out = []
+    for mode in (2, 1):
+        ctx = Q.Context(w.shapes)
+        ctx.qsg_init_samples(w.seed, w.ladders)
+        ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
+        ctx.qsg_sweep(3)
+        out.append([ctx.qsg_get_spins(gi) for gi in range(len(w.shapes))])
+        del ctx
+        torch.cuda.empty_cache()
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
