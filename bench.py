@@ -44,7 +44,56 @@ def parse():
     p.add_argument("--workload", default="L24_Lt2048_hb")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-tune", action="store_true", help="keep the library's default launch options")
+    p.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
+                   help="run one small untimed case for an ncu capture and exit")
     return p.parse_args()
+
+
+# Small untimed cases for ncu captures (a few hundred MB to 2.4 GB on the
+# device, a handful of launches), named by what they exercise.
+def _case_sweep(Q, W):
+    # L=24, L_tau=2048, 128 samples, 1 replica, 32 k: 64 slots, 0.60 GB of state (> L2)
+    ctx = Q.Context([Q.Shape(24, 2048, 128, 1, 32, Q.HEATBATH, Q.PBC)])
+    ctx.qsg_init_samples(3, [W.uniform_ladder(0.22, 0.36, 32)])
+    ctx.qsg_sweep(4)
+    return ctx
+
+
+def _case_measure(Q, W):
+    # L=24, L_tau=2048, 64 samples, 1 replica, 2 k: the correlator kernels at full tile shape
+    ctx = Q.Context([Q.Shape(24, 2048, 64, 1, 2, Q.HEATBATH, Q.PBC)])
+    ctx.qsg_init_samples(3, [W.uniform_ladder(0.22, 0.36, 2)])
+    ctx.qsg_sweep(2)
+    ctx.qsg_measure_correlators()
+    return ctx
+
+
+def _case_step(Q, W):
+    # the bench workload (L=24, L_tau=2048, 128 samples, 4 replicas, 32 k), two
+    # (sweep, tempering) rounds and one measurement: every kernel of a step once or twice
+    w = W.largest()
+    ctx = Q.Context(w.shapes)
+    ctx.qsg_init_samples(w.seed, w.ladders)
+    for _ in range(2):
+        ctx.qsg_sweep(1)
+        ctx.qsg_tempering_swap()
+    ctx.qsg_measure_correlators()
+    return ctx
+
+
+PROFILE_CASES = {"sweep": _case_sweep, "measure": _case_measure, "step": _case_step}
+
+
+def run_profile_case(name):
+    import torch
+
+    from paper_2310_07486_gb300 import qsg as Q
+    from paper_2310_07486_gb300 import workloads as W
+    ctx = PROFILE_CASES[name](Q, W)
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ok", name, flush=True)
 
 
 def dist_env():
@@ -163,6 +212,12 @@ def run_ours(args, rank, world, local):
     ctx.qsg_init_samples(seed, w.ladders)
     sps, nswap, nmeas = step_plan(w)
     updates_per_step = w.spin_updates_per_sweep * sps * nswap
+    # launch options (chunk, register variant, persistent launch, graph batch)
+    # chosen by timing, before the warm-up; the sampled bits do not depend on them
+    tuned = None
+    if not args.no_tune:
+        from paper_2310_07486_gb300 import tuner
+        tuned = tuner.tune(ctx, sweeps_per_call=sps)
 
     sweep_events = []
 
@@ -260,7 +315,8 @@ def run_ours(args, rank, world, local):
                    "step": {"sweeps": sps * nswap, "tempering_steps": nswap, "measurements": nmeas},
                    "spin_updates_per_step": updates_per_step, "state_bytes": 8 * words,
                    "l2": "inputs larger than L2 (state %.2f GB)" % (8 * words / 1e9),
-                   "parallelism": "replicas-only x%d" % world},
+                   "parallelism": "replicas-only x%d" % world,
+                   "launch_options": tuned["options"] if tuned else "library defaults"},
         "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -349,6 +405,9 @@ def run_reference(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world, local)

@@ -174,9 +174,16 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         2 = on: one persistent launch per sweep serves every
  *                         group from a work queue, largest groups first (needs
  *                         one algorithm, L <= 24, every L_tau % 16 == 0)
+ *   QSG_OPT_GRAPH         0 = off; G in 1..4096 = qsg_sweep replays a CUDA
+ *                         graph of G sweeps (captured on first use and again
+ *                         after an option change) for each whole batch of G,
+ *                         and launches the remainder directly.  The graph
+ *                         reads the sweep index from a device counter, so
+ *                         its Philox draws equal those of direct launches.
+ *                         Needs the wavefront kernel for every group.
  * Results do not depend on the options: every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
-       QSG_OPT_PERSISTENT = 5 };
+       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

@@ -63,6 +63,7 @@ struct PlanBuffers {
     Group *groups = nullptr;
     int *order = nullptr, *prefix = nullptr, *chunk = nullptr;
     unsigned *queue = nullptr;
+    uint32_t *sweep_base = nullptr;
 };
 
 // Walk the workspace: when base is null only the size is computed.
@@ -114,7 +115,9 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
     int *pp = (int *)take(sizeof(int) * (ng + 1));
     int *pc = (int *)take(sizeof(int) * ng);
     unsigned *pq = (unsigned *)take(sizeof(unsigned) * 2);
+    uint32_t *psb = (uint32_t *)take(sizeof(uint32_t) * 4);
     if (pb) {
+        pb->sweep_base = psb;
         pb->groups = pg;
         pb->order = po;
         pb->prefix = pp;
@@ -164,7 +167,20 @@ struct qsg_ctx {
     PlanBuffers pb;
     PersistentPlan plan{};
     bool plan_ok = false;
+    // CUDA graph of graph_batch sweeps (QSG_OPT_GRAPH), captured on a private
+    // stream and replayed on `stream`; the kernels read the sweep index from
+    // pb.sweep_base, which base_valid says equals `sweeps`.
+    int graph_batch = 0;
+    long long graph_key = -1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    unsigned long long graph_launches = 0;  // kernels per replay
+    bool base_valid = false;
     std::string last_cuda;
+    ~qsg_ctx() {
+        if (graph_exec) cudaGraphExecDestroy(graph_exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+    }
 };
 
 static qsg_status cuda_fail(qsg_ctx *c, cudaError_t e) {
@@ -335,6 +351,7 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
     ctx->swaps = 0;
     ctx->n_meas = 0;
     ctx->energy_fresh = false;
+    ctx->base_valid = false;
     ctx->initialised = true;
     return QSG_OK;
 }
@@ -359,25 +376,87 @@ qsg_status qsg_set_couplings(qsg_ctx *ctx, int32_t group, const int8_t *J_host) 
     return QSG_OK;
 }
 
+// Launch one sweep of every group; the sweep index is *sb + idx (sb may be null).
+static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t *sb, uint32_t idx, cudaStream_t st) {
+    if (persistent) {
+        QSG_CUDA(ctx, launch_sweep_persistent(ctx->plan, sb, idx, ctx->seed, st));
+        return QSG_OK;
+    }
+    for (const Group &g : ctx->groups) {
+        const int C = ctx->sweep_kernel == 1 ? 0 : wavefront_chunk(g, ctx->chunk);
+        if (C > 0)
+            QSG_CUDA(ctx, launch_sweep_wavefront(g, sb, idx, ctx->seed, g.arrivals, C, st));
+        else if (sb)
+            return QSG_ERR_ARG;  // the reference kernel takes its index by value only
+        else
+            QSG_CUDA(ctx, launch_sweep_reference(g, idx, ctx->seed, st));
+    }
+    return QSG_OK;
+}
+
+// (Re)capture the graph of graph_batch sweeps when a launch option changed.
+static qsg_status ensure_graph(qsg_ctx *ctx, bool persistent) {
+    const long long key = ((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 2 + (persistent ? 1 : 0)) * 2 +
+                           g_wavefront_variant) * 65537LL + ctx->chunk;
+    if (ctx->graph_exec && ctx->graph_key == key) return QSG_OK;
+    if (ctx->graph_exec) {
+        cudaGraphExecDestroy(ctx->graph_exec);
+        ctx->graph_exec = nullptr;
+    }
+    if (!ctx->cap_stream) QSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    const unsigned long long before = g_launches.load();
+    QSG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
+    qsg_status s = QSG_OK;
+    for (int i = 0; i < ctx->graph_batch && s == QSG_OK; ++i)
+        s = launch_one_sweep(ctx, persistent, ctx->pb.sweep_base, (uint32_t)i, ctx->cap_stream);
+    if (s == QSG_OK && launch_add_word(ctx->pb.sweep_base, (uint32_t)ctx->graph_batch, ctx->cap_stream) != cudaSuccess)
+        s = QSG_ERR_CUDA;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(ctx->cap_stream, &graph);
+    const unsigned long long captured = g_launches.load() - before;
+    g_launches.fetch_sub(captured);  // captured launches run only when replayed
+    if (s != QSG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e_end != cudaSuccess) return cuda_fail(ctx, e_end);
+    const cudaError_t e_inst = cudaGraphInstantiate(&ctx->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e_inst != cudaSuccess) {
+        ctx->graph_exec = nullptr;
+        return cuda_fail(ctx, e_inst);
+    }
+    ctx->graph_key = key;
+    ctx->graph_launches = captured;
+    return QSG_OK;
+}
+
 qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
     if (!ctx || n_sweeps < 0) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
     const bool persistent = ctx->plan_ok && ctx->sweep_kernel != 1 &&
                             (ctx->persistent == 2 || (ctx->persistent == 0 && ctx->groups.size() > 1));
-    for (int it = 0; it < n_sweeps && persistent; ++it) {
-        QSG_CUDA(ctx, launch_sweep_persistent(ctx->plan, nullptr, ctx->sweeps, ctx->seed, ctx->stream));
-        ctx->sweeps++;
-    }
-    for (int it = 0; it < n_sweeps && !persistent; ++it) {
-        for (const Group &g : ctx->groups) {
-            const int C = ctx->sweep_kernel == 1 ? 0 : wavefront_chunk(g, ctx->chunk);
-            if (C > 0)
-                QSG_CUDA(ctx, launch_sweep_wavefront(g, nullptr, ctx->sweeps, ctx->seed, g.arrivals, C, ctx->stream));
-            else
-                QSG_CUDA(ctx, launch_sweep_reference(g, ctx->sweeps, ctx->seed, ctx->stream));
+    int done = 0;
+    const int G = ctx->graph_batch;
+    if (G > 0 && n_sweeps >= G) {
+        qsg_status s = ensure_graph(ctx, persistent);
+        if (s != QSG_OK) return s;
+        if (!ctx->base_valid) {
+            QSG_CUDA(ctx, launch_set_word(ctx->pb.sweep_base, ctx->sweeps, ctx->stream));
+            ctx->base_valid = true;
         }
+        for (; done + G <= n_sweeps; done += G) {
+            QSG_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+            count_launches((int)ctx->graph_launches);
+            ctx->sweeps += (uint32_t)G;
+        }
+    }
+    for (; done < n_sweeps; ++done) {
+        qsg_status s = launch_one_sweep(ctx, persistent, nullptr, ctx->sweeps, ctx->stream);
+        if (s != QSG_OK) return s;
         ctx->sweeps++;
+        ctx->base_valid = false;
     }
     if (n_sweeps > 0) ctx->energy_fresh = false;
     return QSG_OK;
@@ -509,6 +588,7 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     ctx->sweeps = sweeps;
+    ctx->base_valid = false;
     ctx->swaps = swaps;
     if (n_meas >= 0) ctx->n_meas = n_meas;
     return QSG_OK;
@@ -521,6 +601,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         if (value == 2)
             for (const Group &g : ctx->groups)
                 if (wavefront_chunk(g, ctx->chunk) == 0) return QSG_ERR_ARG;
+        if (value == 1 && ctx->graph_batch > 0) return QSG_ERR_ARG;
         ctx->sweep_kernel = (int)value;
         return QSG_OK;
     }
@@ -535,6 +616,15 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         ctx->persistent = (int)value;
         return QSG_OK;
     }
+    if (option == QSG_OPT_GRAPH) {
+        if (value < 0 || value > 4096) return QSG_ERR_ARG;
+        if (value > 0 && ctx->sweep_kernel == 1) return QSG_ERR_ARG;
+        if (value > 0)
+            for (const Group &g : ctx->groups)
+                if (wavefront_chunk(g, ctx->chunk) == 0) return QSG_ERR_ARG;
+        ctx->graph_batch = (int)value;
+        return QSG_OK;
+    }
     if (option == QSG_OPT_CORR_KERNEL) {
         if (value < 0 || value > 1) return QSG_ERR_ARG;
         ctx->corr_tensor = value == 0 ? 1 : 0;
@@ -542,7 +632,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
     }
     if (option == QSG_OPT_CHUNK) {
         if (value < 0 || value > 65536) return QSG_ERR_ARG;
-        if (value > 0)
+        if (value > 0 || ctx->graph_batch > 0)
             for (const Group &g : ctx->groups)
                 if (wavefront_chunk(g, (int)value) == 0) return QSG_ERR_ARG;
         ctx->chunk = (int)value;

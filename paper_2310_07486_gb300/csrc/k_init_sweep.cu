@@ -81,11 +81,19 @@ __global__ void k_half_sweep_ref(Group g, int colour, uint32_t sweep, uint32_t k
     }
 }
 
-__global__ void k_set_word(uint32_t *p, uint32_t v) { *p = v; }
+// Device copy of the sweep counter used by replayed graphs: set from the host
+// value before the first replay, advanced by the last node of each replay.
+__global__ void k_set_word(uint32_t *p, uint32_t v, int add) { *p = add ? *p + v : v; }
 
 cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st) {
     count_launches(1);
-    k_set_word<<<1, 1, 0, st>>>(p, value);
+    k_set_word<<<1, 1, 0, st>>>(p, value, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_add_word(uint32_t *p, uint32_t value, cudaStream_t st) {
+    count_launches(1);
+    k_set_word<<<1, 1, 0, st>>>(p, value, 1);
     return cudaGetLastError();
 }
 

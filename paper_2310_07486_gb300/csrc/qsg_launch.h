@@ -29,6 +29,7 @@ extern int g_wavefront_variant;  // 0: register cap for 3 blocks/SM when blocks 
 cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
                                    unsigned *arrivals, int C, cudaStream_t st);
 cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st);
+cudaError_t launch_add_word(uint32_t *p, uint32_t value, cudaStream_t st);
 
 // All groups of a context in one persistent launch per sweep (same algorithm,
 // L <= 24, L_tau % 16 == 0).  Device arrays: the Group structs, the group

@@ -19,7 +19,7 @@ _lib = None
 
 METROPOLIS, HEATBATH = 0, 1
 PBC, APBC = 0, 1
-OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL, OPT_PERSISTENT = 1, 2, 3, 4, 5
+OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL, OPT_PERSISTENT, OPT_GRAPH = 1, 2, 3, 4, 5, 6
 CORR_TENSOR, CORR_INTEGER = 0, 1
 SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 

@@ -325,3 +325,58 @@ def test_ragged_workload_persistent_equals_per_group():
         torch.cuda.empty_cache()
     for a, b in zip(*out):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("persistent", [1, 2])
+def test_graph_replay_equals_direct_launches(persistent):
+    """CUDA-graph replay of batches of sweeps gives the bits of direct launches
+    and of the oracle, across replays, remainders, tempering steps, a counter
+    restore and a recapture after an option change."""
+    shapes = [Q.Shape(8, 32, 70, 2, 3, Q.HEATBATH, Q.PBC), Q.Shape(12, 64, 5, 1, 2, Q.HEATBATH, Q.APBC)]
+    lads = [np.array([0.2, 0.3, 0.4]), np.array([0.25, 0.33])]
+
+    def run(graph):
+        ctx = Q.Context(shapes)
+        ctx.qsg_init_samples(29, lads)
+        ctx.qsg_set_option(Q.OPT_PERSISTENT, persistent)
+        ctx.qsg_set_option(Q.OPT_GRAPH, graph)
+        ctx.qsg_sweep(7)
+        ctx.qsg_tempering_swap()
+        ctx.qsg_sweep(5)
+        ctx.qsg_set_option(Q.OPT_CHUNK, 16)
+        ctx.qsg_sweep(6)
+        sweeps, swaps, _ = ctx.qsg_get_counters()
+        snap = [ctx.qsg_get_spins(gi) for gi in range(len(shapes))]
+        ctx.qsg_sweep(3)
+        ctx.qsg_set_counters(sweeps, swaps, -1)
+        for gi, s in enumerate(snap):
+            ctx.qsg_set_spins(gi, s)
+        ctx.qsg_sweep(4)
+        ctx.qsg_tempering_swap()
+        return [ctx.qsg_get_spins(gi) for gi in range(len(shapes))]
+
+    direct, graphed = run(0), run(3)
+    for a, b in zip(direct, graphed):
+        assert np.array_equal(a, b)
+    for gid, (s, l) in enumerate(zip(shapes, lads)):
+        o = oracle.OracleGroup(s.L, s.Ltau, s.n_samples, s.n_replicas, s.n_k, algo=s.algo, boundary=s.boundary,
+                               group_id=gid)
+        o.init(29, l)
+        o.sweep(7)
+        o.swap()
+        o.sweep(5 + 6 + 4)
+        o.swap()
+        assert np.array_equal(Q.unpack_spins(graphed[gid], s), o.spins()), gid
+
+
+def test_graph_replay_launch_count():
+    shape = Q.Shape(8, 32, 64, 1, 2, Q.METROPOLIS, Q.PBC)
+    ctx = Q.Context([shape])
+    ctx.qsg_init_samples(5, [np.array([0.3, 0.4])])
+    ctx.qsg_set_option(Q.OPT_GRAPH, 4)
+    ctx.qsg_sweep(4)  # capture, counter upload, one replay
+    torch.cuda.synchronize()
+    n0 = Q.qsg_kernel_launches()
+    ctx.qsg_sweep(9)  # two replays of (4 sweeps + counter advance), one direct sweep
+    torch.cuda.synchronize()
+    assert Q.qsg_kernel_launches() - n0 == 2 * 5 + 1
