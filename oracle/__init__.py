@@ -57,6 +57,7 @@ def lib():
             L.orc_measure.argtypes = [vp]
             L.orc_read.argtypes = [vp] * 7
             L.orc_measure_one.argtypes = [vp, i32, i32, i32, vp, vp]
+            L.orc_read_onetime.argtypes = [vp, vp, vp, vp]
             L.orc_get_spins.argtypes = [vp, vp]
             L.orc_set_spins.argtypes = [vp, vp]
             L.orc_get_couplings.argtypes = [vp, vp]
@@ -151,6 +152,24 @@ class OracleGroup:
         Pr = np.zeros((self.n_samples, self.K), dtype=np.int64)
         lib().orc_read(self._h, _ptr(C), _ptr(Q), _ptr(P), _ptr(Cr), _ptr(Qr), _ptr(Pr))
         return dict(C=C, Q2=Q, q2=P, C_raw=Cr, Q2_raw=Qr, q2_raw=Pr)
+
+    ONETIME_SAMPLE_FIELDS = ("q2", "q4", "chi2", "F2", "chi3", "F3", "chi_lin")
+    ONETIME_K_FIELDS = ("chi2", "F2", "xi2", "chi3", "F3", "xi3", "B", "chi_lin")
+
+    def read_onetime(self):
+        """One-time observables: per (sample, k) and disorder-averaged per k,
+        plus the raw integer sums (P4 as a Python int of 128 bits)."""
+        H = self.L // 2
+        ps = np.zeros((self.n_samples, self.K, 7))
+        pk = np.zeros((self.K, 8))
+        raw = np.zeros((self.n_samples, self.K, 4 + 2 * (H + 1)), dtype=np.int64)
+        lib().orc_read_onetime(self._h, _ptr(ps), _ptr(pk), _ptr(raw))
+        out = {f: ps[..., i] for i, f in enumerate(self.ONETIME_SAMPLE_FIELDS)}
+        out["per_k"] = {f: pk[:, i] for i, f in enumerate(self.ONETIME_K_FIELDS)}
+        out["raw"] = raw
+        out["P4"] = [[int(raw[b, j, 1].astype(np.uint64)) + (int(raw[b, j, 2].astype(np.uint64)) << 64)
+                      for j in range(self.K)] for b in range(self.n_samples)]
+        return out
 
     def spins(self):
         S = np.zeros((self.n_samples, self.R, self.K, self.Ltau, self.L, self.L), dtype=np.int8)

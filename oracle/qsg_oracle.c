@@ -58,6 +58,7 @@
 #define ORC_STREAM_INIT 2u
 #define ORC_STREAM_SWEEP 3u
 #define ORC_STREAM_PT 4u
+#define ORC_MAX_TRIPLE_R 8
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two      */
@@ -112,6 +113,10 @@ typedef struct {
     int64_t *Cacc;  /* [R][n_samples][K][n_lag] */
     int64_t *Qacc;  /* [R][n_samples][K][n_lag] */
     int64_t *Pacc;  /* [n_samples][K] */
+    unsigned __int128 *P4acc;  /* [n_samples][K] sum of Q0^4 */
+    int64_t *T3acc; /* [n_samples][K] sum over replica triples of Q_ab Q_bc Q_ca */
+    int64_t *Gacc;  /* [n_samples][K][L/2+1] pair products of momentum sums, by x-distance */
+    int64_t *F3acc; /* [n_samples][K][L/2+1] triple products of momentum sums, by x-distance */
     int64_t *acc;   /* [n_samples][K-1] accepted swaps, summed over replicas */
     int64_t n_meas;
     uint32_t sweep;
@@ -162,9 +167,13 @@ orc_group *orc_create(int L, int Ltau, int n_samples, int R, int K, int algo, in
     g->Cacc = (int64_t *)calloc((size_t)R * ns * K * g->n_lag, sizeof(int64_t));
     g->Qacc = (int64_t *)calloc((size_t)R * ns * K * g->n_lag, sizeof(int64_t));
     g->Pacc = (int64_t *)calloc(ns * K, sizeof(int64_t));
+    g->P4acc = (unsigned __int128 *)calloc(ns * K, sizeof(unsigned __int128));
+    g->T3acc = (int64_t *)calloc(ns * K, sizeof(int64_t));
+    g->Gacc = (int64_t *)calloc(ns * K * (size_t)(L / 2 + 1), sizeof(int64_t));
+    g->F3acc = (int64_t *)calloc(ns * K * (size_t)(L / 2 + 1), sizeof(int64_t));
     g->acc = (int64_t *)calloc(ns * np, sizeof(int64_t));
     if (!g->k || !g->J || !g->S || !g->Tmet || !g->Thb || !g->ptB || !g->ptA || !g->ptA_len ||
-        !g->E || !g->Cacc || !g->Qacc || !g->Pacc || !g->acc)
+        !g->E || !g->Cacc || !g->Qacc || !g->Pacc || !g->P4acc || !g->T3acc || !g->Gacc || !g->F3acc || !g->acc)
         return NULL;
     return g;
 }
@@ -176,7 +185,7 @@ void orc_destroy(orc_group *g)
     for (int i = 0; i < g->n_samples * np; ++i) free(g->ptA[i]);
     free(g->k); free(g->J); free(g->S); free(g->Tmet); free(g->Thb); free(g->ptB);
     free(g->ptA); free(g->ptA_len); free(g->E); free(g->Cacc); free(g->Qacc);
-    free(g->Pacc); free(g->acc); free(g);
+    free(g->Pacc); free(g->P4acc); free(g->T3acc); free(g->Gacc); free(g->F3acc); free(g->acc); free(g);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -282,6 +291,10 @@ int orc_init(orc_group *g, uint64_t seed, const double *ladders, int per_sample,
     memset(g->Cacc, 0, sizeof(int64_t) * (size_t)g->R * g->n_samples * K * g->n_lag);
     memset(g->Qacc, 0, sizeof(int64_t) * (size_t)g->R * g->n_samples * K * g->n_lag);
     memset(g->Pacc, 0, sizeof(int64_t) * (size_t)g->n_samples * K);
+    memset(g->P4acc, 0, sizeof(unsigned __int128) * (size_t)g->n_samples * K);
+    memset(g->T3acc, 0, sizeof(int64_t) * (size_t)g->n_samples * K);
+    memset(g->Gacc, 0, sizeof(int64_t) * (size_t)g->n_samples * K * (g->L / 2 + 1));
+    memset(g->F3acc, 0, sizeof(int64_t) * (size_t)g->n_samples * K * (g->L / 2 + 1));
     memset(g->acc, 0, sizeof(int64_t) * (size_t)g->n_samples * (K > 1 ? K - 1 : 1));
     return 0;
 }
@@ -467,21 +480,81 @@ void orc_measure(orc_group *g)
             g->Qacc[o + lag] += qsum;
         }
     }
-    /* equal-time overlap between replicas at the same ladder position */
+    /* One-time observables, Methods "One-time observables", Eqs. (def-M),
+     * (chi-r), (Binder).  M_xy = <S_x S_y> at equal imaginary time, estimated
+     * with independent replicas a, b, c of the same sample and k, at every
+     * slice tau (the slice is arbitrary, so all of them are averaged):
+     *   Tr M^2          <- Q_ab^2,                  Q_ab = sum_x S^a_x S^b_x
+     *   sum <SSSS>^2    <- Q_ab^4
+     *   Tr M^3          <- Q_ab Q_bc Q_ca
+     *   Tr Mhat M       <- sum_{x,y} S^a_x S^b_x S^a_y S^b_y cos(p (x-y))
+     *   Tr Mhat M^2     <- sum_{x,y} S^s_x S^u_x S^s_y S^v_y cos(p (x-y)) * Q_uv
+     * for p = (2 pi / L, 0) and (0, 2 pi / L).  Pairs (x, y) are grouped by
+     * their distance d = (x1 - y1) mod L along p, so the cosine factors out:
+     * the integer sums per d (folded d ~ L - d) are accumulated and the FP64
+     * finish applies cos(2 pi d / L).  All three choices of the replica s
+     * shared by the two momentum-carrying overlaps are summed. */
 #pragma omp parallel for schedule(dynamic)
     for (int c = 0; c < g->n_samples * K; ++c) {
-        int b = c / K, j = c % K;
-        int64_t sum = 0;
-        for (int ra = 0; ra < R; ++ra)
-            for (int rb = ra + 1; rb < R; ++rb) {
-                const int8_t *A = config(g, b, ra, j), *B = config(g, b, rb, j);
-                for (int t = 0; t < Lt; ++t) {
+        int b = c / K, j = c % K, L = g->L, H = L / 2;
+        int npair = R * (R - 1) / 2;
+        if (npair == 0) continue;
+        int64_t p2 = 0, t3 = 0;
+        unsigned __int128 p4 = 0;
+        int64_t *G = g->Gacc + (size_t)c * (H + 1), *F3 = g->F3acc + (size_t)c * (H + 1);
+        int64_t *Q = (int64_t *)malloc(sizeof(int64_t) * npair);
+        int64_t *nx = (int64_t *)malloc(sizeof(int64_t) * npair * L);  /* column sums over y */
+        int64_t *ny = (int64_t *)malloc(sizeof(int64_t) * npair * L);  /* row sums over x */
+        int *pid = (int *)malloc(sizeof(int) * R * R);
+        for (int t = 0; t < Lt; ++t) {
+            int pi = 0;
+            for (int ra = 0; ra < R; ++ra)
+                for (int rb = ra + 1; rb < R; ++rb, ++pi) {
+                    pid[ra * R + rb] = pid[rb * R + ra] = pi;
+                    const int8_t *A = config(g, b, ra, j) + (size_t)t * L2, *B = config(g, b, rb, j) + (size_t)t * L2;
                     int64_t q = 0;
-                    for (int xy = 0; xy < L2; ++xy) q += A[t * L2 + xy] * B[t * L2 + xy];
-                    sum += q * q;
+                    for (int i = 0; i < L; ++i) { nx[pi * L + i] = 0; ny[pi * L + i] = 0; }
+                    for (int y = 0; y < L; ++y)
+                        for (int x = 0; x < L; ++x) {
+                            int o = A[y * L + x] * B[y * L + x];
+                            q += o;
+                            nx[pi * L + x] += o;
+                            ny[pi * L + y] += o;
+                        }
+                    Q[pi] = q;
+                    p2 += q * q;
+                    p4 += (unsigned __int128)(uint64_t)(q * q) * (uint64_t)(q * q);
+                    for (int c1 = 0; c1 < L; ++c1)
+                        for (int c2 = 0; c2 < L; ++c2) {
+                            int d = ((c2 - c1) % L + L) % L;
+                            if (d > H) d = L - d;
+                            G[d] += nx[pi * L + c1] * nx[pi * L + c2] + ny[pi * L + c1] * ny[pi * L + c2];
+                        }
                 }
-            }
-        g->Pacc[c] += sum;
+            /* three-replica terms for 3 <= R <= ORC_MAX_TRIPLE_R only (their
+             * number grows as R^3; the paper simulates 6 replicas) */
+            for (int ra = 0; ra < R && R <= ORC_MAX_TRIPLE_R; ++ra)
+                for (int rb = ra + 1; rb < R; ++rb)
+                    for (int rc = rb + 1; rc < R; ++rc) {
+                        int ab = pid[ra * R + rb], bc = pid[rb * R + rc], ca = pid[rc * R + ra];
+                        t3 += Q[ab] * Q[bc] * Q[ca];
+                        int rep[3] = {ra, rb, rc};
+                        for (int rot = 0; rot < 3; ++rot) {
+                            int s_ = rep[rot], u = rep[(rot + 1) % 3], v = rep[(rot + 2) % 3];
+                            int su = pid[s_ * R + u], sv = pid[s_ * R + v], uv = pid[u * R + v];
+                            for (int c1 = 0; c1 < L; ++c1)
+                                for (int c2 = 0; c2 < L; ++c2) {
+                                    int d = ((c2 - c1) % L + L) % L;
+                                    if (d > H) d = L - d;
+                                    F3[d] += Q[uv] * (nx[su * L + c1] * nx[sv * L + c2] + ny[su * L + c1] * ny[sv * L + c2]);
+                                }
+                        }
+                    }
+        }
+        g->Pacc[c] += p2;
+        g->P4acc[c] += p4;
+        g->T3acc[c] += t3;
+        free(Q); free(nx); free(ny); free(pid);
     }
     g->n_meas++;
 }
@@ -524,6 +597,87 @@ void orc_read(const orc_group *g, double *C, double *Q, double *P, int64_t *Craw
     for (size_t i = 0; i < np; ++i) {
         if (P) P[i] = (double)g->Pacc[i] / (nm * pairs * L2 * L2 * Lt);
         if (Praw) Praw[i] = g->Pacc[i];
+    }
+}
+
+/* One-time observables of every sample and k (FP64), Eqs. (chi-r), (xi-r),
+ * (Binder), and the linear susceptibility of Sect. "On the magnetic
+ * susceptibilities".  Per (sample b, k j), fields in this order:
+ *   q2   = <Q^2> / L^2D          q4 = <Q^4> / L^4D
+ *   chi2 = <Q^2> / L^D           F2 = <|Q(p)|^2> / L^D (both p averaged)
+ *   chi3 = <Q_ab Q_bc Q_ca> / L^D
+ *   F3   = <Re Q_su(p) Q_sv(-p) Q_uv> / L^D (3 choices of s, both p averaged)
+ *          (chi3 and F3 need 3 <= R <= 8 replicas, NaN otherwise)
+ *   chi_lin = C(0) + 2 sum_{tau=1}^{L_tau/2-1} C(tau) + C(L_tau/2), C averaged
+ *             over replicas (the periodic sum of C over all L_tau slices)
+ * with <.> the average over measurements, slices and replica pairs/triples.
+ * Per k, the disorder averages (mean over the samples of the group):
+ *   chi2, F2, xi2, chi3, F3, xi3, B, chi_lin
+ * with xi = sqrt(chi / F - 1) / (2 sin(pi / L)) and B = mean q4 / (mean q2)^2.
+ * raw (optional): [b][j] = P2, P4 low 64 bits, P4 high 64 bits, T3,
+ * G[0..L/2], F3[0..L/2]. */
+void orc_read_onetime(const orc_group *g, double *per_sample, double *per_k, int64_t *raw)
+{
+    int L = g->L, H = L / 2, K = g->K, R = g->R, ns = g->n_samples, nl = g->n_lag;
+    double LD = (double)(L * L), Lt = (double)g->Ltau, nm = (double)g->n_meas;
+    double npair = (double)(R * (R - 1) / 2), ntrip = (double)(R * (R - 1) * (R - 2) / 6);
+    const double pi = 3.14159265358979323846;
+    for (int b = 0; b < ns; ++b)
+        for (int j = 0; j < K; ++j) {
+            size_t c = (size_t)b * K + j;
+            double G = 0.0, F3 = 0.0;
+            for (int d = 0; d <= H; ++d) {
+                double w = cos(2.0 * pi * d / L);
+                G += w * (double)g->Gacc[c * (H + 1) + d];
+                F3 += w * (double)g->F3acc[c * (H + 1) + d];
+            }
+            double *o = per_sample + c * 7;
+            o[0] = (double)g->Pacc[c] / (nm * npair * LD * LD * Lt);
+            o[1] = (double)g->P4acc[c] / (nm * npair * LD * LD * LD * LD * Lt);
+            o[2] = (double)g->Pacc[c] / (nm * npair * Lt * LD);
+            o[3] = G / (2.0 * nm * npair * Lt * LD);
+            o[4] = (double)g->T3acc[c] / (nm * ntrip * Lt * LD);
+            o[5] = F3 / (6.0 * nm * ntrip * Lt * LD);
+            if (R < 3 || R > ORC_MAX_TRIPLE_R) o[4] = o[5] = NAN;
+            double cl = 0.0;
+            for (int r = 0; r < R; ++r) {
+                const int64_t *Cr = g->Cacc + (((size_t)r * ns + b) * K + j) * nl;
+                double s = 0.0;
+                for (int lag = 0; lag < nl; ++lag) {
+                    double v = (double)Cr[lag] / (nm * LD * Lt);
+                    s += (lag == 0 || lag == nl - 1) ? v : 2.0 * v;
+                }
+                cl += s;
+            }
+            o[6] = cl / R;
+            if (raw) {
+                int64_t *w = raw + c * (4 + 2 * (H + 1));
+                w[0] = g->Pacc[c];
+                w[1] = (int64_t)(uint64_t)g->P4acc[c];
+                w[2] = (int64_t)(uint64_t)(g->P4acc[c] >> 64);
+                w[3] = g->T3acc[c];
+                for (int d = 0; d <= H; ++d) {
+                    w[4 + d] = g->Gacc[c * (H + 1) + d];
+                    w[4 + H + 1 + d] = g->F3acc[c * (H + 1) + d];
+                }
+            }
+        }
+    if (!per_k) return;
+    double s2 = 2.0 * sin(pi / L);
+    for (int j = 0; j < K; ++j) {
+        double m[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int b = 0; b < ns; ++b)
+            for (int f = 0; f < 7; ++f) m[f] += per_sample[((size_t)b * K + j) * 7 + f];
+        for (int f = 0; f < 7; ++f) m[f] /= ns;
+        double *o = per_k + (size_t)j * 8;
+        o[0] = m[2];
+        o[1] = m[3];
+        o[2] = sqrt(m[2] / m[3] - 1.0) / s2;
+        o[3] = m[4];
+        o[4] = m[5];
+        o[5] = sqrt(m[4] / m[5] - 1.0) / s2;
+        o[6] = m[1] / (m[0] * m[0]);
+        o[7] = m[6];
     }
 }
 

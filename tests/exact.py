@@ -101,8 +101,25 @@ def enumerate_states(J, L, Ltau, k, boundary="pbc"):
         s = sl[slices[t]].astype(np.float64)
         M += np.einsum("n,nx,ny->xy", p, s, s)
     M /= Ltau
+    # four-point function at equal time, sum_{xyzu} <S_x S_y S_z S_u>^2 (Eq. (Binder))
+    M4 = np.zeros((L2,) * 4)
+    for t in range(Ltau):
+        s = sl[slices[t]].astype(np.float64)
+        M4 += np.einsum("n,nx,ny,nz,nu->xyzu", p, s, s, s, s)
+    M4 /= Ltau
+    # momentum-space traces with p = (2 pi / L, 0) and (0, 2 pi / L), Eq. (def-M)
+    xs = np.arange(L2) % L
+    ys = np.arange(L2) // L
+    trMhatM, trMhatM2 = [], []
+    for coord in (xs, ys):
+        ph = np.exp(2j * np.pi * coord / L)
+        Mhat = M * ph[:, None] * np.conj(ph)[None, :]
+        trMhatM.append(np.trace(Mhat @ M).real)
+        trMhatM2.append(np.trace(Mhat @ M @ M).real)
     return dict(Z_scaled=Z, Emin=E.min(), E=(p * E).sum(), E2=(p * E * E).sum(), C=C, Q2=Q,
-                logZ=np.log(Z) - k * E.min(), trM2=(M * M).sum() / (L2 * L2))
+                logZ=np.log(Z) - k * E.min(), trM2=(M * M).sum() / (L2 * L2), M=M,
+                chi2=np.trace(M @ M) / L2, chi3=np.trace(M @ M @ M) / L2,
+                F2=np.mean(trMhatM) / L2, F3=np.mean(trMhatM2) / L2, q4=(M4 * M4).sum() / L2 ** 4)
 
 
 def transfer_matrix(J, L, k):

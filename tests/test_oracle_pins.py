@@ -414,3 +414,100 @@ def test_oracle_couplings_are_fair_coins(oracle_lib):
     c = (J[0] * J[1]).mean()
     c2 = (J[0] * J[64]).mean()
     assert abs(c) < 5 / np.sqrt(J[0].size) and abs(c2) < 5 / np.sqrt(J[0].size)
+
+
+# --------------------------------------------------------------------------
+# One-time observables (Methods, "One-time observables"; Eqs. (def-M), (chi-r),
+# (xi-r), (Binder)) and the linear susceptibility
+# --------------------------------------------------------------------------
+def _brute_onetime(S, L):
+    """Direct evaluation of the replica estimators on one configuration set
+    S[r][tau][y][x], with complex exponentials for the momentum sums."""
+    R, Lt = S.shape[0], S.shape[1]
+    N = L * L
+    ph = [np.exp(2j * np.pi * np.arange(L) / L)[None, :], np.exp(2j * np.pi * np.arange(L) / L)[:, None]]
+    pairs = [(a, b) for a in range(R) for b in range(a + 1, R)]
+    trip = [(a, b, c) for a in range(R) for b in range(a + 1, R) for c in range(b + 1, R)]
+    acc = dict(q2=0.0, q4=0, chi2=0.0, F2=0.0, chi3=0.0, F3=0.0)
+    P4 = 0
+    for t in range(Lt):
+        o = {}
+        Q = {}
+        Qp = {}
+        for a, b in pairs:
+            o = S[a, t].astype(np.int64) * S[b, t]
+            Q[a, b] = Q[b, a] = int(o.sum())
+            Qp[a, b] = Qp[b, a] = [(o * ph[d]).sum() for d in range(2)]
+            P4 += Q[a, b] ** 4
+            acc["q2"] += Q[a, b] ** 2
+            acc["F2"] += sum(abs(Qp[a, b][d]) ** 2 for d in range(2)) / 2
+        for a, b, c in trip:
+            acc["chi3"] += Q[a, b] * Q[b, c] * Q[c, a]
+            for s, u, v in ((a, b, c), (b, c, a), (c, a, b)):
+                acc["F3"] += sum((Qp[s, u][d] * np.conj(Qp[s, v][d])).real for d in range(2)) / 2 * Q[u, v] / 3
+    npair, ntrip = len(pairs), max(len(trip), 1)
+    return dict(q2=acc["q2"] / (Lt * npair * N * N), q4=P4 / (Lt * npair * N ** 4), chi2=acc["q2"] / (Lt * npair * N),
+                F2=acc["F2"] / (Lt * npair * N), chi3=acc["chi3"] / (Lt * ntrip * N),
+                F3=acc["F3"] / (Lt * ntrip * N), P4=P4)
+
+
+@pytest.mark.parametrize("L,R", [(4, 3), (6, 4), (2, 3)])
+def test_oracle_onetime_sums_equal_brute_force(oracle_lib, L, R):
+    """One measurement of random configurations: the distance-binned integer
+    sums of the oracle reproduce the complex-exponential definitions."""
+    Lt = 4
+    g = oracle_lib.OracleGroup(L, Lt, 1, R, 1)
+    g.init(5, np.array([0.3]))
+    rng = np.random.default_rng(L * 10 + R)
+    S = (1 - 2 * rng.integers(0, 2, size=(1, R, 1, Lt, L, L))).astype(np.int8)
+    g.set_spins(S)
+    g.measure()
+    got = g.read_onetime()
+    ref = _brute_onetime(S[0, :, 0], L)
+    assert got["P4"][0][0] == ref["P4"]
+    for f in ("q2", "q4", "chi2", "F2", "chi3", "F3"):
+        assert abs(got[f][0, 0] - ref[f]) <= 1e-12 * max(1.0, abs(ref[f])), (f, got[f][0, 0], ref[f])
+
+
+def test_oracle_onetime_matches_exact_traces(oracle_lib):
+    """2x2x4: the replica estimators average to Tr M^2, Tr M^3, Tr(Mhat M),
+    Tr(Mhat M^2) and sum <SSSS>^2 of the exactly enumerated Boltzmann weight."""
+    L, Ltau, k = 2, 4, 0.35
+    J = _rng_couplings(L, 3)
+    ex = exact.enumerate_states(J[0], L, Ltau, k)
+    est = {f: [] for f in ("q2", "q4", "chi2", "F2", "chi3", "F3")}
+    for seed in range(8):
+        g, _ = _run_oracle(oracle_lib, L, Ltau, J, [k], R=4, burn=50, meas=300, seed=2000 + seed)
+        r = g.read_onetime()
+        for f in est:
+            est[f].append(r[f][0, 0])
+    exp = dict(q2=ex["trM2"], q4=ex["q4"], chi2=ex["chi2"], F2=ex["F2"], chi3=ex["chi3"], F3=ex["F3"])
+    for f, v in est.items():
+        z = _z(np.array(v), exp[f])
+        assert z < 5, (f, np.mean(v), exp[f])
+    # F differs from chi at this k (the check is not vacuous)
+    assert abs(ex["F2"] - ex["chi2"]) > 0.05
+
+
+def test_oracle_onetime_decoupled_closed_form(oracle_lib):
+    """J = 0: distinct sites are independent, so M = identity: chi = F = 1
+    (xi = 0 up to noise), the Binder ratio is 3 - 2 / L^D exactly, and the
+    linear susceptibility is the periodic sum of the chain correlator."""
+    L, Ltau, k, ns = 4, 8, 0.4, 4
+    J = np.zeros((ns, 2, L, L), dtype=np.int8)
+    res = []
+    for seed in range(6):
+        g = oracle_lib.OracleGroup(L, Ltau, ns, 4, 1, algo="heatbath")
+        g.init(3000 + seed, np.array([k]), couplings=J)
+        g.sweep(50)
+        for _ in range(150):
+            g.sweep(1)
+            g.measure()
+        res.append(g.read_onetime()["per_k"])
+    t = np.tanh(k)
+    lag = np.arange(Ltau)
+    chi_lin = ((t ** lag + t ** (Ltau - lag)) / (1 + t ** Ltau)).sum()
+    for f, v in (("chi2", 1.0), ("F2", 1.0), ("chi3", 1.0), ("F3", 1.0), ("B", 3 - 2 / (L * L)),
+                 ("chi_lin", chi_lin)):
+        z = _z(np.array([r[f][0] for r in res]), v)
+        assert z < 5, (f, [r[f][0] for r in res], v)
