@@ -127,7 +127,17 @@ qsg_status qsg_tempering_swap(qsg_ctx *ctx);
  * c = sum_x S_x,tau1 S_x,tau1+tau (s = -1 when tau1+tau wraps under APBC), and
  *   P_acc[b][j] += sum_{r<r'} sum_tau1 (sum_x S^r_x,tau1 S^r'_x,tau1)^2
  * for tau = 0 .. L_tau/2 (Eqs. (C_A_transfer), (def-C-Q2-tau); the replica
- * overlap is the Tr M^2 / L^2D comparator of the Q2 plateau). */
+ * overlap is the Tr M^2 / L^2D comparator of the Q2 plateau).
+ * The same pass accumulates the one-time sums (Methods, "One-time
+ * observables", Eqs. (def-M), (chi-r), (Binder)) over slices tau and replica
+ * pairs / triples, with Q_ab = sum_x S^a_x S^b_x and n_c the overlap summed
+ * over column (row) c of the slice:
+ *   P4[b][j]   += Q_ab^4                                   (128-bit exact)
+ *   G[b][j][d] += sum_c n_c (n_{c+d} + n_{c-d})  both directions, d = 0 .. L/2
+ *                 (a single term at d = 0 and d = L/2)
+ *   T3[b][j]   += Q_ab Q_bc Q_ca                            (3 <= R <= 8)
+ *   F3[b][j][d] += Q_uv sum_c n^su_c (n^sv_{c+d} + n^sv_{c-d}), s = a, b, c
+ * unless QSG_OPT_ONETIME = 1 turned the three-replica sums off. */
 qsg_status qsg_measure_correlators(qsg_ctx *ctx);
 
 /* FP64 finish of one group on the device (Eq. (def-C-Q2-tau)):
@@ -137,6 +147,25 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx);
  * q2 [n_samples][K] (any may be NULL).  raw (optional, host int64) receives
  * C_acc then Q_acc then P_acc in the same layouts.  Synchronises the stream. */
 qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw);
+
+/* One-time observables of one group (Methods, "One-time observables";
+ * Eqs. (chi-r), (xi-r), (Binder)) and the linear susceptibility (Sect. "On the
+ * magnetic susceptibilities"), finished in FP64 on the device from the sums
+ * of qsg_measure_correlators (N = L^2 sites, p = 2 pi / L along x and y):
+ *   per_sample [n_samples][K][7]: q2 = <Q^2>/N^2, q4 = <Q^4>/N^4,
+ *     chi2 = <Q^2>/N, F2 = <|Q(p)|^2>/N, chi3 = <Q_ab Q_bc Q_ca>/N,
+ *     F3 = <Re Q_su(p) Q_sv(-p) Q_uv>/N, chi_lin = C(0) + 2 sum_{0<tau<L_tau/2}
+ *     C(tau) + C(L_tau/2) (C averaged over replicas), where <.> averages
+ *     measurements, slices and replica pairs (triples; both p and the three
+ *     choices of s for F); chi3 and F3 are NaN unless 3 <= R <= 8 and the
+ *     three-replica sums are on;
+ *   per_k [K][8]: disorder averages over the group's samples of chi2, F2, then
+ *     xi2 = sqrt(chi2/F2 - 1) / (2 sin(pi/L)), chi3, F3, xi3 likewise,
+ *     B = mean q4 / (mean q2)^2, and chi_lin;
+ *   raw (host int64) [n_samples][K][4 + 2 (L/2+1)]: sum Q^2, sum Q^4 as low
+ *     then high 64 bits of a 128-bit integer, T3, G[0..L/2], F3[0..L/2].
+ * Any output may be NULL.  Synchronises the stream. */
+qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, double *per_k, int64_t *raw);
 
 /* Action E of every configuration, host int64 [n_samples][R][K] (ladder
  * position j).  Computes it if no sweep fused it.  Synchronises the stream. */
@@ -181,9 +210,12 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         reads the sweep index from a device counter, so
  *                         its Philox draws equal those of direct launches.
  *                         Needs the wavefront kernel for every group.
+ *   QSG_OPT_ONETIME       0 = accumulate every one-time sum (default),
+ *                         1 = skip the three-replica sums (chi3, F3 become
+ *                         NaN); only before the first measurement
  * Results do not depend on the options: every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
-       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6 };
+       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

@@ -51,6 +51,7 @@ Group describe(const qsg_shape &s, int gid) {
     g.nlag = s.Ltau / 2 + 1;
     g.n_samples = s.n_samples;
     g.nwx = (s.L * s.L + 63) / 64;
+    g.xi_norm = 2.0 * std::sin(3.14159265358979323846 / s.L);
     return g;
 }
 
@@ -97,6 +98,14 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
         g.outC = (double *)take(sizeof(double) * nc);
         g.outQ = (double *)take(sizeof(double) * nc);
         g.outP = (double *)take(sizeof(double) * (size_t)g.W * 64 * g.K);
+        const size_t nsk = (size_t)g.W * 64 * g.K, nd = (size_t)(g.L / 2 + 1);
+        g.P4acc = (unsigned long long *)take(sizeof(unsigned long long) * 2 * nsk);
+        g.T3acc = (long long *)take(sizeof(long long) * nsk);
+        g.Gacc = (long long *)take(sizeof(long long) * nsk * nd);
+        g.F3acc = (long long *)take(sizeof(long long) * nsk * nd);
+        g.outO = (double *)take(sizeof(double) * nsk * 7);
+        g.outK = (double *)take(sizeof(double) * (size_t)g.K * 8);
+        g.wcos = (double *)take(sizeof(double) * nd);
         g.arrivals = (unsigned *)take(sizeof(unsigned) * (size_t)g.nslots * (g.Ltau / 4 > 0 ? g.Ltau / 4 : 1));
         // one (w, j) pair at least, up to the cap
         const size_t per = measure_scratch_words_per_pair(g);
@@ -164,6 +173,7 @@ struct qsg_ctx {
     int chunk = 0;         // QSG_OPT_CHUNK
     int corr_tensor = 1;   // QSG_OPT_CORR_KERNEL: 1 tensor cores, 0 integer pipes
     int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 on
+    int triples = 1;       // QSG_OPT_ONETIME: 1 with the three-replica sums, 0 without
     PlanBuffers pb;
     PersistentPlan plan{};
     bool plan_ok = false;
@@ -291,6 +301,7 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
     std::vector<std::vector<uint32_t>> thr(ctx->groups.size());
     std::vector<std::vector<uint64_t>> A(ctx->groups.size()), B(ctx->groups.size());
     std::vector<std::vector<int32_t>> Aoff(ctx->groups.size()), Alen(ctx->groups.size());
+    std::vector<std::vector<double>> wcos(ctx->groups.size());
     const double *lad = k_ladders;
     for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
         const Group &g = ctx->groups[gi];
@@ -298,6 +309,8 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
             if (!(lad[j] > 0.0) || !(lad[j] < 3.0)) return QSG_ERR_ARG;
             if (j > 0 && !(lad[j] > lad[j - 1])) return QSG_ERR_ARG;
         }
+        // cos(2 pi d / L) of the momentum sums of the one-time observables
+        for (int d = 0; d <= g.L / 2; ++d) wcos[gi].push_back(std::cos(2.0 * 3.14159265358979323846 * d / g.L));
         thr[gi].assign(16 * (size_t)g.K, 0u);
         for (int j = 0; j < g.K; ++j) {
             for (int c = 0; c < 3; ++c) thr[gi][16 * j + c] = met_threshold(lad[j], 2 * (c + 1));
@@ -343,6 +356,12 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
         QSG_CUDA(ctx, cudaMemsetAsync(g.Cacc, 0, sizeof(long long) * nc, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.Qacc, 0, sizeof(long long) * nc, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.Pacc, 0, sizeof(long long) * (size_t)g.W * 64 * g.K, st));
+        const size_t nsk = (size_t)g.W * 64 * g.K, nd = (size_t)(g.L / 2 + 1);
+        QSG_CUDA(ctx, cudaMemsetAsync(g.P4acc, 0, sizeof(unsigned long long) * 2 * nsk, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.T3acc, 0, sizeof(long long) * nsk, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.Gacc, 0, sizeof(long long) * nsk * nd, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.F3acc, 0, sizeof(long long) * nsk * nd, st));
+        QSG_CUDA(ctx, cudaMemcpyAsync(g.wcos, wcos[gi].data(), sizeof(double) * nd, cudaMemcpyHostToDevice, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.acc, 0, sizeof(unsigned long long) * (size_t)g.W * 64 * np, st));
     }
     // host copies of the tables must stay alive until the copies complete
@@ -483,7 +502,8 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     for (const Group &g : ctx->groups)
-        QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->corr_tensor, ctx->d_err, ctx->stream));
+        QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->corr_tensor, ctx->triples, ctx->d_err,
+                                     ctx->stream));
     ctx->n_meas++;
     return QSG_OK;
 }
@@ -525,6 +545,55 @@ qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *
     for (int b = 0; b < S; ++b) {
         if (q2) std::memcpy(q2 + (size_t)b * K, hp.data() + (size_t)b * K, sizeof(double) * K);
         if (raw) std::memcpy(raw + 2 * outc + (size_t)b * K, rp.data() + (size_t)b * K, sizeof(long long) * K);
+    }
+    return QSG_OK;
+}
+
+qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, double *per_k, int64_t *raw) {
+    if (!ctx || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    const size_t nsk = (size_t)g.W * 64 * g.K, nd = (size_t)(g.L / 2 + 1);
+    QSG_CUDA(ctx, launch_onetime_finish(g, ctx->n_meas, ctx->triples, ctx->stream));
+    std::vector<double> ho(nsk * 7), hk((size_t)g.K * 8);
+    std::vector<long long> rp, rt, rg, rf;
+    std::vector<unsigned long long> r4;
+    QSG_CUDA(ctx, cudaMemcpyAsync(ho.data(), g.outO, sizeof(double) * ho.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaMemcpyAsync(hk.data(), g.outK, sizeof(double) * hk.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    if (raw) {
+        rp.resize(nsk);
+        rt.resize(nsk);
+        r4.resize(2 * nsk);
+        rg.resize(nsk * nd);
+        rf.resize(nsk * nd);
+        QSG_CUDA(ctx, cudaMemcpyAsync(rp.data(), g.Pacc, sizeof(long long) * nsk, cudaMemcpyDeviceToHost, ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(rt.data(), g.T3acc, sizeof(long long) * nsk, cudaMemcpyDeviceToHost, ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(r4.data(), g.P4acc, sizeof(unsigned long long) * 2 * nsk, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(rg.data(), g.Gacc, sizeof(long long) * nsk * nd, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        QSG_CUDA(ctx, cudaMemcpyAsync(rf.data(), g.F3acc, sizeof(long long) * nsk * nd, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    }
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const size_t ns = (size_t)g.n_samples * g.K;
+    if (per_sample) std::memcpy(per_sample, ho.data(), sizeof(double) * ns * 7);
+    if (per_k) std::memcpy(per_k, hk.data(), sizeof(double) * hk.size());
+    if (raw) {
+        const size_t rw = 4 + 2 * nd;
+        for (size_t c = 0; c < ns; ++c) {
+            int64_t *o = raw + c * rw;
+            // sum of Q^4 = high part * 2^32 + low part, as a 128-bit integer
+            const unsigned __int128 p4 = ((unsigned __int128)r4[2 * c + 1] << 32) + (unsigned __int128)r4[2 * c];
+            o[0] = rp[c];
+            o[1] = (int64_t)(uint64_t)p4;
+            o[2] = (int64_t)(uint64_t)(p4 >> 64);
+            o[3] = rt[c];
+            for (size_t d = 0; d < nd; ++d) {
+                o[4 + d] = rg[c * nd + d];
+                o[4 + nd + d] = rf[c * nd + d];
+            }
+        }
     }
     return QSG_OK;
 }
@@ -623,6 +692,14 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
             for (const Group &g : ctx->groups)
                 if (wavefront_chunk(g, ctx->chunk) == 0) return QSG_ERR_ARG;
         ctx->graph_batch = (int)value;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_ONETIME) {
+        if (value < 0 || value > 1) return QSG_ERR_ARG;
+        // the three-replica sums accumulate only while enabled: changing it
+        // between measurements would mix counts, so it must precede the first
+        if (ctx->n_meas > 0 && (value == 0) != (ctx->triples == 1)) return QSG_ERR_STATE;
+        ctx->triples = value == 0 ? 1 : 0;
         return QSG_OK;
     }
     if (option == QSG_OPT_CORR_KERNEL) {

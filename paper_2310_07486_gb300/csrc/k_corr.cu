@@ -89,38 +89,8 @@ __global__ void __launch_bounds__(256) k_gram(Group g, int p0, const uint64_t *P
 }
 
 // Equal-time overlap of every replica pair at one ladder position.
-__global__ void __launch_bounds__(256) k_overlap(Group g, int p0, const uint64_t *P) {
-    __shared__ long long red[256 / 32];
-    const int pb = blockIdx.x / 64, b = blockIdx.x % 64;
-    const int p = p0 + pb, w = p / g.K, j = p % g.K;
-    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L;
-    const size_t plane = (size_t)Lt * nwx;
-    long long sum = 0;
-    for (int t = threadIdx.x; t < Lt; t += blockDim.x) {
-        for (int ra = 0; ra < g.R; ++ra) {
-            const uint64_t *A = P + (((size_t)pb * g.R + ra) * 64 + b) * plane + (size_t)t * nwx;
-            for (int rb = ra + 1; rb < g.R; ++rb) {
-                const uint64_t *B = P + (((size_t)pb * g.R + rb) * 64 + b) * plane + (size_t)t * nwx;
-                int d = 0;
-                for (int x = 0; x < nwx; ++x) d += __popcll(A[x] ^ B[x]);
-                const long long q = (long long)(L2 - 2 * d);
-                sum += q * q;
-            }
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long tot = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot += red[i];
-        g.Pacc[((size_t)w * 64 + b) * g.K + j] += tot;
-    }
-}
-
-cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int *status,
-                           cudaStream_t st) {
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int triples,
+                           int *status, cudaStream_t st) {
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
     if (batch < 1) return cudaErrorInvalidValue;
@@ -146,12 +116,9 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return e;
-        if (g.R >= 2) {
-            count_launches(1);
-            k_overlap<<<np * 64, 256, 0, st>>>(g, p0, scratch);
-            e = cudaGetLastError();
-            if (e != cudaSuccess) return e;
-        }
+        // equal-time replica overlaps and the other one-time sums (k_onetime.cu)
+        e = launch_onetime(g, p0, np, scratch, triples, st);
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

@@ -29,8 +29,15 @@ struct Group {
     uint32_t *swapmask;  // [W*R][K-1][2] 32-bit halves of the per-pair swap masks
     unsigned long long *acc;  // [W*64][K-1] accepted swaps (summed over replicas)
     long long *Cacc, *Qacc;   // [R][W*64][K][nlag]
-    long long *Pacc;          // [W*64][K]
+    long long *Pacc;          // [W*64][K]  sum of Q_ab^2 over slices and replica pairs
+    unsigned long long *P4acc;  // [W*64][K][2] sum of Q_ab^4: low 32 bits and high bits summed apart
+    long long *T3acc;         // [W*64][K] sum of Q_ab Q_bc Q_ca over slices and replica triples
+    long long *Gacc, *F3acc;  // [W*64][K][L/2+1] momentum sums binned by x-distance
     double *outC, *outQ, *outP;
+    double *outO;             // [W*64][K][7] one-time observables of every sample
+    double *outK;             // [K][8] disorder averages
+    double *wcos;             // [L/2+1] cos(2 pi d / L), host FP64
+    double xi_norm;           // 2 sin(pi / L), host FP64
     unsigned *arrivals;  // [nslots][L_tau/4] boundary arrival counters of the wavefront sweep
 };
 

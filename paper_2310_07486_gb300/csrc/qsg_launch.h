@@ -54,8 +54,13 @@ cudaError_t launch_tempering(const Group &g, uint32_t m, uint64_t seed, cudaStre
 // tensor = 1 computes the Gram tiles with tcgen05 (k_corr_tc.cu), 0 with
 // XOR/popcount on the integer pipes.  status receives DEVERR_TIMEOUT if a
 // bounded wait of the tensor path gave up.
-cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int *status,
-                           cudaStream_t st);
+// triples = 1 also accumulates the three-replica one-time sums (3 <= R <= 8).
+cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int triples,
+                           int *status, cudaStream_t st);
+// One-time observable sums of a batch of (w, j) pairs from the transposed scratch.
+cudaError_t launch_onetime(const Group &g, int p0, int np, const uint64_t *P, int triples, cudaStream_t st);
+// FP64 finish of the one-time observables into g.outO and g.outK.
+cudaError_t launch_onetime_finish(const Group &g, long long n_meas, int triples, cudaStream_t st);
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st);
 
 // FP64 finish into g.outC / g.outQ / g.outP.

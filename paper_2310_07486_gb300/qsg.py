@@ -19,7 +19,8 @@ _lib = None
 
 METROPOLIS, HEATBATH = 0, 1
 PBC, APBC = 0, 1
-OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL, OPT_PERSISTENT, OPT_GRAPH = 1, 2, 3, 4, 5, 6
+OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL, OPT_PERSISTENT, OPT_GRAPH, OPT_ONETIME = \
+    1, 2, 3, 4, 5, 6, 7
 CORR_TENSOR, CORR_INTEGER = 0, 1
 SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 
@@ -71,6 +72,8 @@ def load_library(path: str | None = None):
     lib.qsg_read_correlators.restype = i32
     lib.qsg_read_correlators.argtypes = [vp, i32, vp, vp, vp, vp]
     lib.qsg_read_energies.restype = i32
+    lib.qsg_read_onetime.argtypes = [vp, i32, vp, vp, vp]
+    lib.qsg_read_onetime.restype = i32
     lib.qsg_read_energies.argtypes = [vp, i32, vp]
     lib.qsg_read_accepts.restype = i32
     lib.qsg_read_accepts.argtypes = [vp, i32, vp]
@@ -244,6 +247,21 @@ class Context:
         if raw:
             out.update(C_raw=R[:nc].reshape(shp), Q2_raw=R[nc:2 * nc].reshape(shp),
                        q2_raw=R[2 * nc:].reshape(s.n_samples, s.n_k))
+        return out
+
+    ONETIME_SAMPLE_FIELDS = ("q2", "q4", "chi2", "F2", "chi3", "F3", "chi_lin")
+    ONETIME_K_FIELDS = ("chi2", "F2", "xi2", "chi3", "F3", "xi3", "B", "chi_lin")
+
+    def qsg_read_onetime(self, group=0):
+        s = self.shapes[group]
+        H = s.L // 2
+        ps = np.zeros((s.n_samples, s.n_k, 7))
+        pk = np.zeros((s.n_k, 8))
+        raw = np.zeros((s.n_samples, s.n_k, 4 + 2 * (H + 1)), dtype=np.int64)
+        self._check(self.lib.qsg_read_onetime(self.h, group, _ptr(ps), _ptr(pk), _ptr(raw)), "qsg_read_onetime")
+        out = {f: ps[..., i] for i, f in enumerate(self.ONETIME_SAMPLE_FIELDS)}
+        out["per_k"] = {f: pk[:, i] for i, f in enumerate(self.ONETIME_K_FIELDS)}
+        out["raw"] = raw
         return out
 
     def qsg_read_energies(self, group=0):

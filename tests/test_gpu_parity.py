@@ -380,3 +380,56 @@ def test_graph_replay_launch_count():
     ctx.qsg_sweep(9)  # two replays of (4 sweeps + counter advance), one direct sweep
     torch.cuda.synchronize()
     assert Q.qsg_kernel_launches() - n0 == 2 * 5 + 1
+
+
+def _close_nan(a, b, rtol=RTOL):
+    a, b = np.asarray(a), np.asarray(b)
+    both = np.isnan(a) & np.isnan(b)
+    return np.all(both | (np.abs(a - b) <= rtol * np.maximum(np.abs(b), 1e-300)))
+
+
+@pytest.mark.parametrize("L,Ltau,ns,R,K,boundary", [(6, 12, 70, 3, 2, Q.PBC), (8, 16, 64, 4, 2, Q.APBC),
+                                                     (4, 8, 5, 2, 3, Q.PBC), (10, 8, 3, 9, 1, Q.PBC),
+                                                     (2, 6, 64, 5, 2, Q.PBC)])
+def test_onetime_observables_match_oracle(L, Ltau, ns, R, K, boundary):
+    """Integer one-time sums bit for bit, FP64 per-sample and per-k values to
+    1e-12 (R = 2: no triples; R = 9: beyond the three-replica limit)."""
+    shape = Q.Shape(L, Ltau, ns, R, K, Q.HEATBATH, boundary)
+    lad = np.linspace(0.25, 0.4, K)
+    ctx, orc = _pair(shape, lad, seed=41)
+    for _ in range(3):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        ctx.qsg_measure_correlators()
+        orc.measure()
+    got, ref = ctx.qsg_read_onetime(), orc.read_onetime()
+    assert np.array_equal(got["raw"], ref["raw"])
+    for f in Q.Context.ONETIME_SAMPLE_FIELDS:
+        assert _close_nan(got[f], ref[f]), f
+    for f in Q.Context.ONETIME_K_FIELDS:
+        assert _close_nan(got["per_k"][f], ref["per_k"][f]), f
+    if R < 3 or R > 8:
+        assert np.all(np.isnan(got["chi3"]))
+    else:
+        assert np.all(np.isfinite(got["chi3"]))
+
+
+def test_onetime_without_triples_keeps_pair_sums():
+    shape = Q.Shape(8, 16, 64, 4, 2, Q.METROPOLIS, Q.PBC)
+    outs = []
+    for opt in (0, 1):
+        ctx = Q.Context([shape])
+        ctx.qsg_init_samples(43, [np.array([0.3, 0.35])])
+        ctx.qsg_set_option(Q.OPT_ONETIME, opt)
+        ctx.qsg_sweep(3)
+        ctx.qsg_measure_correlators()
+        outs.append(ctx.qsg_read_onetime())
+        if opt == 1:
+            with pytest.raises(Q.QSGError):
+                ctx.qsg_set_option(Q.OPT_ONETIME, 0)  # after a measurement
+    a, b = outs
+    for f in ("q2", "q4", "chi2", "F2", "chi_lin"):
+        assert np.array_equal(a[f], b[f])
+    assert np.all(np.isnan(b["chi3"])) and np.all(np.isfinite(a["chi3"]))
