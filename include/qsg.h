@@ -167,6 +167,33 @@ qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *
  * Any output may be NULL.  Synchronises the stream. */
 qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, double *per_k, int64_t *raw);
 
+/* Per-sample correlation lengths (Methods, "Fitting process and Euclidean
+ * correlation length estimation"), host FP64, no device work.
+ * C, Q2: host [n_replicas][n_series][L_tau/2+1], e.g. the outputs of
+ * qsg_read_correlators with n_series = n_samples * K.  For every series:
+ * replica mean and standard error; Q2 plateau = weighted constant on
+ * [L_tau/4, L_tau/2] (acceptable iff chi2/dof <= 2); windows tau_w = first lag
+ * >= 1 where C (resp. Q2 - plateau) <= 3.5 sigma (Q2: L_tau/2 and the plateau
+ * free when the constant fit is not acceptable; C: eta not estimated when C
+ * never gets there); C fitted to B [e^{-tau/eta} + z e^{-(L_tau-tau)/eta}]
+ * (z = +1 PBC, -1 APBC) on [tau_min, tau_w], tau_min from tau_w/10 up until
+ * chi2/dof < 1; Q2 fitted to the plateau plus one and plus two exponentials,
+ * tau_min from 1 up until chi2/dof < 0.5, the smaller chi2/dof kept and eta_e
+ * its largest decay length.  Diagonal covariance; errors from (J^T W J)^-1.
+ * n_replicas >= 2, L_tau >= 4 even.  out: caller-owned [n_series]. */
+typedef struct {
+    int32_t C_ok, C_tau_w, C_tau_min, Q_ok;
+    int32_t Q_tau_w, Q_tau_min, Q_n_exp, plateau_ok;
+    double eta, eta_err, C_amp, C_chi2dof;
+    double Q_pl, Q_pl_err, plateau_chi2dof, eta_e, eta_e_err, eta_2, Q_chi2dof;
+} qsg_fit_result;
+qsg_status qsg_fit_correlators(const double *C, const double *Q2, int32_t n_replicas, int64_t n_series,
+                               int32_t Ltau, int32_t boundary, qsg_fit_result *out);
+
+/* tilde tau = (L_tau / pi) sin(pi tau / L_tau) for tau = 0 .. L_tau/2 (Sect. "On
+ * the magnetic susceptibilities"), into host out[L_tau/2+1]. */
+void qsg_tau_tilde(int32_t Ltau, double *out);
+
 /* Action E of every configuration, host int64 [n_samples][R][K] (ladder
  * position j).  Computes it if no sweep fused it.  Synchronises the stream. */
 qsg_status qsg_read_energies(qsg_ctx *ctx, int32_t group, int64_t *E_host);

@@ -3,8 +3,17 @@ and Euclidean correlation length estimation") and of the tau-tilde variable
 of Sect. "On the magnetic susceptibilities".
 
 TEST INFRASTRUCTURE ONLY: loaded by the tests and nothing else.  It shares no
-code with the library's fits (csrc/fits.cpp); scipy's least-squares solver
-stands in as the minimiser step, which the paper does not specify.
+code with the library's fits (csrc/fits.cpp).
+
+The paper does not name its minimiser.  Both sides read it as Marquardt's
+damped Gauss-Newton (Levenberg-Marquardt): damping lambda = 1e-3 to start,
+the normal matrix's diagonal scaled by (1 + lambda), lambda x10 after a
+rejected step (chi2 not lower, or a decay length not positive), /10 after an
+accepted one (not below 1e-15); stop when an accepted step is below 1e-14 of
+every parameter, when chi2 falls by less than 1e-15 of itself, after 2000
+iterations or when lambda exceeds 1e30.  Following the same iteration from
+the same start, two-exponential fits reach the same one of their several
+minima on both sides.
 
 Steps, in the paper's order, for one sample at one k given the correlators of
 its R replicas at lags 0 .. L_tau/2:
@@ -29,7 +38,6 @@ from __future__ import annotations
 import math
 
 import numpy as np
-from scipy.optimize import least_squares
 
 PLATEAU_CHI2 = 2.0
 WINDOW_SIGMAS = 3.5
@@ -83,20 +91,46 @@ def _loglin_guess(tau, y):
     return (float(y[ok][0]) if ok.any() else 1.0), max(1.0, (tau[-1] - tau[0]) / 2)
 
 
-def _lsq(model, jac, p0, tau, y, s):
-    def res(p):
-        return (model(p, tau) - y) / s
+def _lsq(model, jac, p0, tau, y, s, valid):
+    """Levenberg-Marquardt minimisation of sum ((model - y) / s)^2."""
+    w = 1.0 / s ** 2
 
-    def jres(p):
-        return jac(p, tau) / s[:, None]
+    def chi2_of(p):
+        return float((w * (model(p, tau) - y) ** 2).sum())
 
-    r = least_squares(res, p0, jac=jres, method="lm", xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
-    p = r.x
-    chi2 = float((res(p) ** 2).sum())
-    Jw = jres(p)
+    def normal(p):
+        J = jac(p, tau)
+        r = model(p, tau) - y
+        return (J * w[:, None]).T @ J, (J * w[:, None]).T @ r
+
+    p = np.array(p0, dtype=np.float64)
+    chi2 = chi2_of(p)
+    lam = 1e-3
+    A, g = normal(p)
+    it = 0
+    while it < 2000 and lam < 1e30:
+        it += 1
+        diag = np.where(np.diag(A) > 0, np.diag(A), 1.0)
+        M = A + lam * np.diag(diag)
+        try:
+            step = np.linalg.solve(M, -g)
+        except np.linalg.LinAlgError:
+            lam *= 10.0
+            continue
+        trial = p + step
+        c2 = chi2_of(trial) if valid(trial) else math.inf
+        if not c2 < chi2:
+            lam *= 10.0
+            continue
+        small = bool(np.all(np.abs(step) <= 1e-14 * (np.abs(p) + 1e-14)))
+        flat = chi2 - c2 <= 1e-15 * chi2
+        p, chi2 = trial, c2
+        lam = max(lam * 0.1, 1e-15)
+        A, g = normal(p)
+        if small or flat:
+            break
     try:
-        cov = np.linalg.inv(Jw.T @ Jw)
-        err = np.sqrt(np.abs(np.diag(cov)))
+        err = np.sqrt(np.abs(np.diag(np.linalg.inv(A))))
     except np.linalg.LinAlgError:
         err = np.full(len(p), np.nan)
     return p, err, chi2
@@ -127,7 +161,8 @@ def fit_C(C, s, Ltau, zeta):
         if dof < 1:
             return out
         B0, eta0 = _loglin_guess(tau.astype(float), C[tau])
-        p, err, chi2 = _lsq(model, jac, np.array([B0, eta0]), tau.astype(float), C[tau], s[tau])
+        p, err, chi2 = _lsq(model, jac, np.array([B0, eta0]), tau.astype(float), C[tau], s[tau],
+                            lambda q: q[1] > 0)
         if p[1] > 0 and chi2 / dof < C_CHI2:
             out.update(ok=True, eta=float(p[1]), eta_err=float(err[1]), B=float(p[0]), chi2dof=chi2 / dof,
                        tau_min=int(tmin))
@@ -170,8 +205,9 @@ def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl):
         else:
             q0 = [0.5 * B0, 2.0 * eta0, 0.5 * B0, 0.5 * eta0]
         p0 = np.array(([base] if free_pl else []) + q0)
-        p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau])
-        etas = p[(1 if free_pl else 0) + 1::2]
+        off = 1 if free_pl else 0
+        p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau], lambda q: bool(np.all(q[off + 1::2] > 0)))
+        etas = p[off + 1::2]
         if np.all(etas > 0) and chi2 / dof < Q_CHI2:
             return chi2 / dof, p, err, int(tmin)
     return None

@@ -1,6 +1,6 @@
 """Build the sm_103a shared library ``libqsg.so`` in-tree with nvcc.
 
-Each CUDA translation unit is compiled in parallel to an object file, then the
+Each CUDA (and host C++) translation unit is compiled in parallel to an object file, then the
 objects are linked into ``paper_2310_07486_gb300/_build/libqsg.so``.  Only the
 ``compute_103a``/``sm_103a`` target is generated.
 """
@@ -38,13 +38,13 @@ def _stale(target, deps):
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    sources = sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     objs = []
     jobs = []
     for src in sources:
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(BUILD, os.path.splitext(os.path.basename(src))[0] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
             cmd = [nvcc()] + ARCH + FLAGS + list(extra) + ["-c", src, "-o", obj]

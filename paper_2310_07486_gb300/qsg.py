@@ -75,6 +75,10 @@ def load_library(path: str | None = None):
     lib.qsg_read_onetime.argtypes = [vp, i32, vp, vp, vp]
     lib.qsg_read_onetime.restype = i32
     lib.qsg_read_energies.argtypes = [vp, i32, vp]
+    lib.qsg_fit_correlators.restype = i32
+    lib.qsg_fit_correlators.argtypes = [vp, vp, i32, ctypes.c_int64, i32, i32, vp]
+    lib.qsg_tau_tilde.restype = None
+    lib.qsg_tau_tilde.argtypes = [i32, vp]
     lib.qsg_read_accepts.restype = i32
     lib.qsg_read_accepts.argtypes = [vp, i32, vp]
     lib.qsg_get_spins.restype = i32
@@ -298,6 +302,33 @@ class Context:
 
     def qsg_set_counters(self, sweeps, swaps, n_meas=-1):
         self._check(self.lib.qsg_set_counters(self.h, int(sweeps), int(swaps), int(n_meas)), "qsg_set_counters")
+
+
+class qsg_fit_result(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("C_ok", "C_tau_w", "C_tau_min", "Q_ok", "Q_tau_w", "Q_tau_min",
+                                                "Q_n_exp", "plateau_ok")] + \
+               [(n, ctypes.c_double) for n in ("eta", "eta_err", "C_amp", "C_chi2dof", "Q_pl", "Q_pl_err",
+                                                 "plateau_chi2dof", "eta_e", "eta_e_err", "eta_2", "Q_chi2dof")]
+
+
+def qsg_fit_correlators(C, Q2, Ltau, boundary=PBC):
+    """Fits of every series of C, Q2 [R][n_series][L_tau/2+1] (the layout of
+    qsg_read_correlators with the sample and k axes merged); list of dicts."""
+    C = np.ascontiguousarray(C, dtype=np.float64)
+    Q2 = np.ascontiguousarray(Q2, dtype=np.float64)
+    R, n = C.shape[0], int(np.prod(C.shape[1:-1]))
+    out = (qsg_fit_result * max(n, 1))()
+    st = load_library().qsg_fit_correlators(_ptr(C), _ptr(Q2), R, n, int(Ltau), int(boundary),
+                                             ctypes.cast(out, ctypes.c_void_p))
+    if st != 0:
+        raise QSGError(st, "qsg_fit_correlators")
+    return [{f: getattr(out[i], f) for f, _ in qsg_fit_result._fields_} for i in range(n)]
+
+
+def qsg_tau_tilde(Ltau):
+    out = np.zeros(Ltau // 2 + 1)
+    load_library().qsg_tau_tilde(int(Ltau), _ptr(out))
+    return out
 
 
 # ---- host-side layout helpers (no method arithmetic) -----------------------
