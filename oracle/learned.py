@@ -1,0 +1,246 @@
+"""Oracle of the learned-ladder part: per-sample coupling features, the MLP
+(64 -> 128 -> 128 -> 33, ReLU) with its loss and gradients in FP64, its BF16
+inference, Adam, and the log-binning thermalisation judge.
+
+TEST INFRASTRUCTURE ONLY: loaded by the tests and nothing else; it shares no
+code with the library's kernels (csrc/k_features.cu, csrc/k_mlp.cu,
+csrc/judge.cpp).  The paper has no learned component; the definitions below
+are this project's, stated once here and in the library's header.
+
+Couplings J[2][L][L] (+-1): J[0][y][x] couples (x,y)-(x+1,y), J[1][y][x]
+couples (x,y)-(x,y+1), periodic.  The plaquette at (x,y) has corners (x,y),
+(x+1,y), (x,y+1), (x+1,y+1); it is frustrated when the product of its four
+bonds J[0][y][x] J[1][y][x+1] J[0][y+1][x] J[1][y][x] is -1.
+
+Features (64, each a count divided by its number of cases, computed in FP64
+and rounded once to FP32):
+   0      fraction of frustrated plaquettes
+   1-5    sites by the sum of their four bonds: -4, -2, 0, 2, 4
+   6-10   sites by the number of frustrated plaquettes among the four touching them: 0..4
+   11-15  2x2 blocks of plaquettes (corners at even x, y) by frustrated count: 0..4
+   16-31  frustrated fraction in each cell of a 4x4 coarse grid
+          (cell (floor(4x/L), floor(4y/L)), index 16 + 4 cy + cx; empty cells 0)
+   32, 33 frustrated pairs at diagonal offsets (+1,+1) and (+1,-1), per plaquette
+   34, 35 fraction of negative x bonds, of negative y bonds
+   36-41  plaquette rows by frustrated fraction, 6 bins [i/6, (i+1)/6) (last closed)
+   42-47  plaquette columns likewise
+   48-55  frustrated pairs at offset (d, 0), d = 1..8 (mod L), per plaquette
+   56-63  frustrated pairs at offset (0, d), d = 1..8
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+N_FEAT, N_H, N_OUT = 64, 128, 33
+# parameter vector: W1 [128][64], b1 [128], W2 [128][128], b2 [128], W3 [33][128], b3 [33]
+SHAPES = [(N_H, N_FEAT), (N_H,), (N_H, N_H), (N_H,), (N_OUT, N_H), (N_OUT,)]
+N_PARAMS = sum(int(np.prod(s)) for s in SHAPES)
+
+
+# --------------------------------------------------------------------------
+# features
+# --------------------------------------------------------------------------
+def frustration(J):
+    L = J.shape[-1]
+    F = np.zeros((L, L), dtype=np.int64)
+    for y in range(L):
+        for x in range(L):
+            p = int(J[0, y, x]) * int(J[1, y, (x + 1) % L]) * int(J[0, (y + 1) % L, x]) * int(J[1, y, x])
+            F[y, x] = 1 if p < 0 else 0
+    return F
+
+
+def features(J):
+    """The 64 features of one sample's couplings J[2][L][L]."""
+    J = np.asarray(J, dtype=np.int64)
+    L = J.shape[-1]
+    F = frustration(J)
+    n = L * L
+    f = np.zeros(N_FEAT, dtype=np.float64)
+    f[0] = F.sum() / n
+    for y in range(L):
+        for x in range(L):
+            s = J[0, y, x] + J[0, y, (x - 1) % L] + J[1, y, x] + J[1, (y - 1) % L, x]
+            f[1 + (s + 4) // 2] += 1
+            c = F[y, x] + F[y, (x - 1) % L] + F[(y - 1) % L, x] + F[(y - 1) % L, (x - 1) % L]
+            f[6 + c] += 1
+    f[1:11] /= n
+    nb = 0
+    for y in range(0, L - 1, 2):
+        for x in range(0, L - 1, 2):
+            f[11 + F[y, x] + F[y, x + 1] + F[y + 1, x] + F[y + 1, x + 1]] += 1
+            nb += 1
+    if nb:
+        f[11:16] /= nb
+    cnt = np.zeros(16)
+    tot = np.zeros(16)
+    for y in range(L):
+        for x in range(L):
+            c = (4 * y // L) * 4 + (4 * x // L)
+            cnt[c] += F[y, x]
+            tot[c] += 1
+    f[16:32] = np.where(tot > 0, cnt / np.maximum(tot, 1), 0.0)
+    d1 = d2 = 0
+    for y in range(L):
+        for x in range(L):
+            d1 += F[y, x] * F[(y + 1) % L, (x + 1) % L]
+            d2 += F[y, x] * F[(y - 1) % L, (x + 1) % L]
+    f[32], f[33] = d1 / n, d2 / n
+    f[34] = (J[0] < 0).sum() / n
+    f[35] = (J[1] < 0).sum() / n
+    for y in range(L):
+        f[36 + min(int(6 * F[y, :].sum() // L), 5)] += 1
+    for x in range(L):
+        f[42 + min(int(6 * F[:, x].sum() // L), 5)] += 1
+    f[36:48] /= L
+    for d in range(1, 9):
+        f[47 + d] = sum(F[y, x] * F[y, (x + d) % L] for y in range(L) for x in range(L)) / n
+        f[55 + d] = sum(F[y, x] * F[(y + d) % L, x] for y in range(L) for x in range(L)) / n
+    return f.astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# MLP in FP64
+# --------------------------------------------------------------------------
+def unpack(theta):
+    out, o = [], 0
+    for s in SHAPES:
+        k = int(np.prod(s))
+        out.append(np.asarray(theta[o:o + k], dtype=np.float64).reshape(s))
+        o += k
+    return out
+
+
+def pack(parts):
+    return np.concatenate([np.asarray(p, dtype=np.float64).ravel() for p in parts])
+
+
+def init_params(seed):
+    """He-uniform weights, zero biases (seeded host draw, an input of both sides)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for s in SHAPES:
+        if len(s) == 2:
+            lim = math.sqrt(6.0 / s[1])
+            parts.append(rng.uniform(-lim, lim, size=s))
+        else:
+            parts.append(np.zeros(s))
+    return pack(parts).astype(np.float32)
+
+
+def forward(theta, X):
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    X = np.asarray(X, dtype=np.float64)
+    z1 = X @ W1.T + b1
+    h1 = np.maximum(z1, 0)
+    z2 = h1 @ W2.T + b2
+    h2 = np.maximum(z2, 0)
+    y = h2 @ W3.T + b3
+    return y, (X, z1, h1, z2, h2)
+
+
+def loss_and_grad(theta, X, T):
+    """Mean over the batch of: cross-entropy between softmax(y[0:32]) and the
+    target fractions T[0:32], plus (y[32] - T[32])^2.  Returns (loss, grad)."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    T = np.asarray(T, dtype=np.float64)
+    B = T.shape[0]
+    y, (X, z1, h1, z2, h2) = forward(theta, X)
+    a = y[:, :32]
+    a = a - a.max(axis=1, keepdims=True)
+    lse = np.log(np.exp(a).sum(axis=1, keepdims=True))
+    logp = a - lse
+    ce = -(T[:, :32] * logp).sum(axis=1)
+    r = y[:, 32] - T[:, 32]
+    loss = float((ce + r * r).mean())
+    dy = np.zeros_like(y)
+    p = np.exp(logp)
+    dy[:, :32] = (p * T[:, :32].sum(axis=1, keepdims=True) - T[:, :32]) / B
+    dy[:, 32] = 2 * r / B
+    gW3 = dy.T @ h2
+    gb3 = dy.sum(0)
+    dh2 = dy @ W3
+    dz2 = dh2 * (z2 > 0)
+    gW2 = dz2.T @ h1
+    gb2 = dz2.sum(0)
+    dh1 = dz2 @ W2
+    dz1 = dh1 * (z1 > 0)
+    gW1 = dz1.T @ X
+    gb1 = dz1.sum(0)
+    return loss, pack([gW1, gb1, gW2, gb2, gW3, gb3])
+
+
+def adam(theta, m, v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015) at step number t >= 1, in FP64."""
+    m = b1 * m + (1 - b1) * g
+    v = b2 * v + (1 - b2) * g * g
+    mh = m / (1 - b1 ** t)
+    vh = v / (1 - b2 ** t)
+    return theta - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def to_bf16(a):
+    """Round FP32 values to bfloat16 (nearest, ties to even), returned as FP64."""
+    u = np.asarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(theta, X):
+    """Inference with BF16 weights, inputs and hidden activations, exact
+    products and sums (FP64 here), outputs not rounded."""
+    W1, b1, W2, b2, W3, b3 = [to_bf16(p) for p in unpack(theta)]
+    h = to_bf16(X)
+    h = to_bf16(np.maximum(h @ W1.T + b1, 0))
+    h = to_bf16(np.maximum(h @ W2.T + b2, 0))
+    return h @ W3.T + b3
+
+
+def ladder_from_output(y, k_min, k_max):
+    """k_j = k_min + (k_max - k_min) sum_{i<=j} softmax(y[0:32])_i; budget 2^(16 y[32])."""
+    a = np.asarray(y[:32], dtype=np.float64)
+    p = np.exp(a - a.max())
+    p /= p.sum()
+    return k_min + (k_max - k_min) * np.cumsum(p), 2.0 ** (16.0 * float(y[32]))
+
+
+# --------------------------------------------------------------------------
+# log-binning judge
+# --------------------------------------------------------------------------
+def judge(E_bins, q_bins, n_last=3):
+    """First bin at which a sample counts as thermalised, or -1.
+
+    E_bins [n_bins][n_samples][R][K]: per replica, the mean energy per site over
+    the tempering steps of bin m (sweeps in [2^m, 2^(m+1))).
+    q_bins [n_bins][n_samples][K][n_pairs]: per replica pair, the mean q^2 of
+    the measurements of bin m.
+    Bin m passes when, for every k, each of the bins m-1 .. m-n_last+1 agrees
+    with bin m within one combined standard error, for the energy (error =
+    replica spread) and for q^2 (error = pair spread)."""
+    E_bins = np.asarray(E_bins, dtype=np.float64)
+    q_bins = np.asarray(q_bins, dtype=np.float64)
+    nb, ns = E_bins.shape[0], E_bins.shape[1]
+    out = np.full(ns, -1, dtype=np.int64)
+
+    def stats(a):  # mean and standard error over the last axis
+        n = a.shape[-1]
+        m = a.mean(axis=-1)
+        se = np.sqrt(((a - m[..., None]) ** 2).sum(axis=-1) / (n * (n - 1)))
+        return m, se
+
+    Em, Es = stats(np.swapaxes(E_bins, 2, 3))  # [nb][ns][K]
+    qm, qs = stats(q_bins)                      # [nb][ns][K]
+    for b in range(ns):
+        for m in range(n_last - 1, nb):
+            ok = True
+            for i in range(1, n_last):
+                for mean, se in ((Em, Es), (qm, qs)):
+                    d = np.abs(mean[m, b] - mean[m - i, b])
+                    if np.any(d > np.sqrt(se[m, b] ** 2 + se[m - i, b] ** 2)):
+                        ok = False
+            if ok:
+                out[b] = m
+                break
+    return out
