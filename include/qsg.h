@@ -194,6 +194,83 @@ qsg_status qsg_fit_correlators(const double *C, const double *Q2, int32_t n_repl
  * the magnetic susceptibilities"), into host out[L_tau/2+1]. */
 void qsg_tau_tilde(int32_t Ltau, double *out);
 
+/* Sum over measurements and slices of Q_ab^2 = (sum_x S^a_x S^b_x)^2 for every
+ * replica pair a < b, pairs ordered (0,1), (0,2), ..., (R-2,R-1): host int64
+ * [n_samples][K][R(R-1)/2] (the per-pair form of the q2 accumulator, used by
+ * the thermalisation judge).  Synchronises the stream. */
+qsg_status qsg_read_pair_overlaps(qsg_ctx *ctx, int32_t group, int64_t *out);
+
+/* ---------------------------------------------------------------------------
+ * Learned k ladder.  The paper has no learned component; these entry points
+ * predict a sample's k-ladder spacing and sweep budget from its couplings,
+ * with the plain uniform ladder as fallback and the log-binning judge below
+ * deciding thermalisation, so the physics results do not depend on them.
+ * ------------------------------------------------------------------------- */
+
+/* The 64 coupling features of every sample of one group, host float
+ * [n_samples][64], computed on the device from the coupling bit-planes.  A
+ * plaquette (x,y) with corners (x,y), (x+1,y), (x,y+1), (x+1,y+1) is frustrated
+ * when an odd number of its four bonds is negative.  Each feature is a count
+ * over its number of cases, divided in FP64 and rounded once to FP32:
+ *   0      frustrated plaquettes
+ *   1-5    sites by the sum of their four bonds -4, -2, 0, 2, 4
+ *   6-10   sites by the number (0..4) of frustrated plaquettes touching them
+ *   11-15  2x2 plaquette blocks at even (x, y) by frustrated count 0..4
+ *   16-31  frustrated fraction of each cell (floor(4x/L), floor(4y/L)) of a 4x4
+ *          coarse grid, index 16 + 4 cy + cx (0 for empty cells)
+ *   32, 33 frustrated pairs at offsets (+1,+1), (+1,-1)
+ *   34, 35 negative x bonds, negative y bonds
+ *   36-41  plaquette rows by frustrated fraction, bins [i/6, (i+1)/6), last closed
+ *   42-47  plaquette columns likewise
+ *   48-55  frustrated pairs at offsets (d, 0), d = 1..8 (mod L)
+ *   56-63  frustrated pairs at offsets (0, d)
+ * Uses the correlator scratch of the context.  Synchronises the stream. */
+qsg_status qsg_sample_features(qsg_ctx *ctx, int32_t group, float *out);
+
+/* The predictor: a 64 -> 128 -> 128 -> 33 ReLU MLP, FP32 parameters in the
+ * order W1[128][64], b1[128], W2[128][128], b2[128], W3[33][128], b3[33]
+ * (qsg_mlp_param_count() = 29089).  Outputs: y[0..31] -> softmax -> fractions
+ * f_i of the ladder, k_j = k_min + (k_max - k_min) sum_{i<=j} f_i; y[32] =
+ * log2(sweep budget) / 16.  Loss of a batch: mean over its samples of the
+ * cross-entropy between softmax(y[0:32]) and the targets t[0:32], plus
+ * (y[32] - t[32])^2.  Training: Adam (0.9, 0.999, 1e-8), deterministic.
+ * Inference in FP32 or BF16 (weights, inputs and hidden activations rounded
+ * to bfloat16 nearest-even, FP32 products and sums).
+ * The caller allocates the device workspace (qsg_mlp_workspace_bytes) for up
+ * to n_data training samples (and prediction inputs) and batches of at most
+ * max_batch (<= 4096) samples; the handle never allocates device memory. */
+typedef struct qsg_mlp qsg_mlp;
+int32_t qsg_mlp_param_count(void);
+size_t qsg_mlp_workspace_bytes(int64_t n_data, int32_t max_batch);
+qsg_status qsg_mlp_create(qsg_mlp **out, void *d_workspace, size_t workspace_bytes, int64_t n_data,
+                          int32_t max_batch, void *cuda_stream);
+void qsg_mlp_destroy(qsg_mlp *mlp);
+/* Host float [param_count]; set also clears the Adam state.  Both synchronise. */
+qsg_status qsg_mlp_set_params(qsg_mlp *mlp, const float *host);
+qsg_status qsg_mlp_get_params(qsg_mlp *mlp, float *host);
+/* Training set: host float X [n][64] (features), T [n][33] (targets). */
+qsg_status qsg_mlp_set_data(qsg_mlp *mlp, const float *X, const float *T, int64_t n);
+/* Loss and gradient (host float [param_count], may be NULL) of the batch of
+ * training-set rows idx[0..batch), without updating the parameters. */
+qsg_status qsg_mlp_grad(qsg_mlp *mlp, const int32_t *idx, int32_t batch, float *loss, float *grad);
+/* `steps` Adam steps with learning rate lr, step s on the rows
+ * idx[s*batch .. (s+1)*batch); losses (host float [steps], may be NULL)
+ * receives each step's batch loss before its update. */
+qsg_status qsg_mlp_train(qsg_mlp *mlp, const int32_t *idx, int32_t steps, int32_t batch, float lr, float *losses);
+/* Outputs Y (host float [n][33]) for inputs X (host float [n][64]), n <= n_data. */
+qsg_status qsg_mlp_predict(qsg_mlp *mlp, const float *X, int64_t n, int32_t bf16, float *Y);
+
+/* Log-binning thermalisation judge (host FP64).  Bins of sweeps
+ * [2^m, 2^(m+1)); E_bins [n_bins][n_samples][n_replicas][n_k]: per replica,
+ * the bin mean of the energy per site; q_bins [n_bins][n_samples][n_k][n_pairs]:
+ * per replica pair, the bin mean of q^2.  Each replica's (pair's) values are
+ * averaged over the k values; first_pass[b] (host int32 [n_samples]) = the
+ * first bin m >= n_last - 1 such that each of bins m-1 .. m-n_last+1 agrees
+ * with bin m within one combined standard error (over replicas for E, over
+ * pairs for q^2), or -1.  n_replicas, n_pairs, n_last >= 2. */
+qsg_status qsg_judge(const double *E_bins, const double *q_bins, int32_t n_bins, int32_t n_samples,
+                     int32_t n_replicas, int32_t n_k, int32_t n_pairs, int32_t n_last, int32_t *first_pass);
+
 /* Action E of every configuration, host int64 [n_samples][R][K] (ladder
  * position j).  Computes it if no sweep fused it.  Synchronises the stream. */
 qsg_status qsg_read_energies(qsg_ctx *ctx, int32_t group, int64_t *E_host);

@@ -58,6 +58,7 @@ def lib():
             L.orc_read.argtypes = [vp] * 7
             L.orc_measure_one.argtypes = [vp, i32, i32, i32, vp, vp]
             L.orc_read_onetime.argtypes = [vp, vp, vp, vp]
+            L.orc_read_pair_overlaps.argtypes = [vp, vp]
             L.orc_get_spins.argtypes = [vp, vp]
             L.orc_set_spins.argtypes = [vp, vp]
             L.orc_get_couplings.argtypes = [vp, vp]
@@ -169,6 +170,11 @@ class OracleGroup:
         out["raw"] = raw
         out["P4"] = [[int(raw[b, j, 1].astype(np.uint64)) + (int(raw[b, j, 2].astype(np.uint64)) << 64)
                       for j in range(self.K)] for b in range(self.n_samples)]
+        return out
+
+    def read_pair_overlaps(self):
+        out = np.zeros((self.n_samples, self.K, self.R * (self.R - 1) // 2), dtype=np.int64)
+        lib().orc_read_pair_overlaps(self._h, _ptr(out))
         return out
 
     def spins(self):

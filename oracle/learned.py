@@ -216,9 +216,10 @@ def judge(E_bins, q_bins, n_last=3):
     the tempering steps of bin m (sweeps in [2^m, 2^(m+1))).
     q_bins [n_bins][n_samples][K][n_pairs]: per replica pair, the mean q^2 of
     the measurements of bin m.
-    Bin m passes when, for every k, each of the bins m-1 .. m-n_last+1 agrees
-    with bin m within one combined standard error, for the energy (error =
-    replica spread) and for q^2 (error = pair spread)."""
+    Each replica's (pair's) bin means are averaged over the K ladder points;
+    bin m passes when each of the bins m-1 .. m-n_last+1 agrees with it within
+    one combined standard error (sqrt(se_m^2 + se_i^2), se over replicas for
+    the energy and over pairs for q^2)."""
     E_bins = np.asarray(E_bins, dtype=np.float64)
     q_bins = np.asarray(q_bins, dtype=np.float64)
     nb, ns = E_bins.shape[0], E_bins.shape[1]
@@ -230,15 +231,14 @@ def judge(E_bins, q_bins, n_last=3):
         se = np.sqrt(((a - m[..., None]) ** 2).sum(axis=-1) / (n * (n - 1)))
         return m, se
 
-    Em, Es = stats(np.swapaxes(E_bins, 2, 3))  # [nb][ns][K]
-    qm, qs = stats(q_bins)                      # [nb][ns][K]
+    Em, Es = stats(E_bins.mean(axis=3))            # per replica, k-averaged: [nb][ns]
+    qm, qs = stats(q_bins.mean(axis=2))            # per pair, k-averaged: [nb][ns]
     for b in range(ns):
         for m in range(n_last - 1, nb):
             ok = True
             for i in range(1, n_last):
                 for mean, se in ((Em, Es), (qm, qs)):
-                    d = np.abs(mean[m, b] - mean[m - i, b])
-                    if np.any(d > np.sqrt(se[m, b] ** 2 + se[m - i, b] ** 2)):
+                    if abs(mean[m, b] - mean[m - i, b]) > np.sqrt(se[m, b] ** 2 + se[m - i, b] ** 2):
                         ok = False
             if ok:
                 out[b] = m

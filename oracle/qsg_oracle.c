@@ -117,6 +117,7 @@ typedef struct {
     int64_t *T3acc; /* [n_samples][K] sum over replica triples of Q_ab Q_bc Q_ca */
     int64_t *Gacc;  /* [n_samples][K][L/2+1] pair products of momentum sums, by x-distance */
     int64_t *F3acc; /* [n_samples][K][L/2+1] triple products of momentum sums, by x-distance */
+    int64_t *PPacc; /* [n_samples][K][R(R-1)/2] sum of Q_ab^2 of each replica pair a < b */
     int64_t *acc;   /* [n_samples][K-1] accepted swaps, summed over replicas */
     int64_t n_meas;
     uint32_t sweep;
@@ -171,9 +172,10 @@ orc_group *orc_create(int L, int Ltau, int n_samples, int R, int K, int algo, in
     g->T3acc = (int64_t *)calloc(ns * K, sizeof(int64_t));
     g->Gacc = (int64_t *)calloc(ns * K * (size_t)(L / 2 + 1), sizeof(int64_t));
     g->F3acc = (int64_t *)calloc(ns * K * (size_t)(L / 2 + 1), sizeof(int64_t));
+    g->PPacc = (int64_t *)calloc(ns * K * (size_t)(R * (R - 1) / 2 + 1), sizeof(int64_t));
     g->acc = (int64_t *)calloc(ns * np, sizeof(int64_t));
     if (!g->k || !g->J || !g->S || !g->Tmet || !g->Thb || !g->ptB || !g->ptA || !g->ptA_len ||
-        !g->E || !g->Cacc || !g->Qacc || !g->Pacc || !g->P4acc || !g->T3acc || !g->Gacc || !g->F3acc || !g->acc)
+        !g->E || !g->Cacc || !g->Qacc || !g->Pacc || !g->P4acc || !g->T3acc || !g->Gacc || !g->F3acc || !g->PPacc || !g->acc)
         return NULL;
     return g;
 }
@@ -185,7 +187,7 @@ void orc_destroy(orc_group *g)
     for (int i = 0; i < g->n_samples * np; ++i) free(g->ptA[i]);
     free(g->k); free(g->J); free(g->S); free(g->Tmet); free(g->Thb); free(g->ptB);
     free(g->ptA); free(g->ptA_len); free(g->E); free(g->Cacc); free(g->Qacc);
-    free(g->Pacc); free(g->P4acc); free(g->T3acc); free(g->Gacc); free(g->F3acc); free(g->acc); free(g);
+    free(g->Pacc); free(g->P4acc); free(g->T3acc); free(g->Gacc); free(g->F3acc); free(g->PPacc); free(g->acc); free(g);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -295,6 +297,7 @@ int orc_init(orc_group *g, uint64_t seed, const double *ladders, int per_sample,
     memset(g->T3acc, 0, sizeof(int64_t) * (size_t)g->n_samples * K);
     memset(g->Gacc, 0, sizeof(int64_t) * (size_t)g->n_samples * K * (g->L / 2 + 1));
     memset(g->F3acc, 0, sizeof(int64_t) * (size_t)g->n_samples * K * (g->L / 2 + 1));
+    memset(g->PPacc, 0, sizeof(int64_t) * (size_t)g->n_samples * K * (g->R * (g->R - 1) / 2 + 1));
     memset(g->acc, 0, sizeof(int64_t) * (size_t)g->n_samples * (K > 1 ? K - 1 : 1));
     return 0;
 }
@@ -523,6 +526,7 @@ void orc_measure(orc_group *g)
                         }
                     Q[pi] = q;
                     p2 += q * q;
+                    g->PPacc[(size_t)c * npair + pi] += q * q;
                     p4 += (unsigned __int128)(uint64_t)(q * q) * (uint64_t)(q * q);
                     for (int c1 = 0; c1 < L; ++c1)
                         for (int c2 = 0; c2 < L; ++c2) {
@@ -679,6 +683,13 @@ void orc_read_onetime(const orc_group *g, double *per_sample, double *per_k, int
         o[6] = m[1] / (m[0] * m[0]);
         o[7] = m[6];
     }
+}
+
+/* Sum over measurements and slices of Q_ab^2 for each replica pair a < b
+ * (pairs in the order (0,1), (0,2), ..., (R-2,R-1)): out [n_samples][K][pairs]. */
+void orc_read_pair_overlaps(const orc_group *g, int64_t *out)
+{
+    memcpy(out, g->PPacc, sizeof(int64_t) * (size_t)g->n_samples * g->K * (g->R * (g->R - 1) / 2));
 }
 
 /* ------------------------------------------------------------------------ */

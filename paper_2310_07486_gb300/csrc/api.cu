@@ -103,6 +103,7 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
         g.T3acc = (long long *)take(sizeof(long long) * nsk);
         g.Gacc = (long long *)take(sizeof(long long) * nsk * nd);
         g.F3acc = (long long *)take(sizeof(long long) * nsk * nd);
+        g.PPacc = (long long *)take(sizeof(long long) * nsk * (size_t)(g.R * (g.R - 1) / 2 + 1));
         g.outO = (double *)take(sizeof(double) * nsk * 7);
         g.outK = (double *)take(sizeof(double) * (size_t)g.K * 8);
         g.wcos = (double *)take(sizeof(double) * nd);
@@ -113,6 +114,9 @@ size_t carve(std::vector<Group> &gs, char *base, int **err, uint64_t **scratch, 
         if (want < per) want = per;
         const size_t all = per * (size_t)g.W * g.K;
         if (want > all) want = all;
+        // the scratch also holds the coupling features, [W*64][64] float
+        const size_t feat = (size_t)g.W * 64 * 64 / 2;
+        if (want < feat) want = feat;
         if (want > sw) sw = want;
     }
     *scratch = (uint64_t *)take(sizeof(uint64_t) * sw);
@@ -361,6 +365,7 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
         QSG_CUDA(ctx, cudaMemsetAsync(g.T3acc, 0, sizeof(long long) * nsk, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.Gacc, 0, sizeof(long long) * nsk * nd, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.F3acc, 0, sizeof(long long) * nsk * nd, st));
+        QSG_CUDA(ctx, cudaMemsetAsync(g.PPacc, 0, sizeof(long long) * nsk * (size_t)(g.R * (g.R - 1) / 2 + 1), st));
         QSG_CUDA(ctx, cudaMemcpyAsync(g.wcos, wcos[gi].data(), sizeof(double) * nd, cudaMemcpyHostToDevice, st));
         QSG_CUDA(ctx, cudaMemsetAsync(g.acc, 0, sizeof(unsigned long long) * (size_t)g.W * 64 * np, st));
     }
@@ -595,6 +600,32 @@ qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, dou
             }
         }
     }
+    return QSG_OK;
+}
+
+qsg_status qsg_read_pair_overlaps(qsg_ctx *ctx, int32_t group, int64_t *out) {
+    if (!ctx || !out || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    const size_t np = (size_t)(g.R * (g.R - 1) / 2);
+    if (np == 0) return QSG_OK;
+    QSG_CUDA(ctx, cudaMemcpyAsync(out, g.PPacc, sizeof(long long) * (size_t)g.n_samples * g.K * np,
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return QSG_OK;
+}
+
+qsg_status qsg_sample_features(qsg_ctx *ctx, int32_t group, float *out) {
+    if (!ctx || !out || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    const Group &g = ctx->groups[group];
+    // the correlator scratch is free between calls: it holds the features
+    if (ctx->scratch_words * sizeof(uint64_t) < (size_t)g.W * 64 * 64 * sizeof(float)) return QSG_ERR_WORKSPACE;
+    float *d = reinterpret_cast<float *>(ctx->scratch);
+    QSG_CUDA(ctx, launch_features(g, d, ctx->stream));
+    QSG_CUDA(ctx, cudaMemcpyAsync(out, d, sizeof(float) * (size_t)g.n_samples * 64, cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    QSG_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     return QSG_OK;
 }
 

@@ -77,8 +77,12 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
     const int R = g.R, Lt = g.Ltau, bd = blockDim.x, tid = threadIdx.x;
     const int npair = R * (R - 1) / 2;
     const bool do3 = triples && R >= 3 && R <= kMaxTripleR;
-    int8_t *nsh = reinterpret_cast<int8_t *>(ot_smem);                             // [pair][dir][c][thread]
-    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + (size_t)npair * 2 * L * bd);  // [pair][thread]
+    // [pair] per-pair sums of Q^2, then (triples only) [pair][dir][c][thread] and [pair][thread]
+    unsigned long long *ppsh = reinterpret_cast<unsigned long long *>(ot_smem);
+    int8_t *nsh = reinterpret_cast<int8_t *>(ot_smem + (size_t)npair * 8);
+    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + (size_t)npair * 8 + (size_t)npair * 2 * L * bd);
+    for (int i = tid; i < npair; i += bd) ppsh[i] = 0ull;
+    __syncthreads();
     const int pb = blockIdx.x / 64, b = blockIdx.x % 64;
     const int p = p0 + pb, w = p / g.K, j = p % g.K;
     const size_t plane = (size_t)Lt * NW;
@@ -105,6 +109,7 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
                 for (int r = 0; r < L; ++r) q0 += ny[r];
                 const unsigned long long q2 = (unsigned long long)(q0 * q0);
                 p2 += (long long)q2;
+                atomicAdd(&ppsh[pi], q2);
                 const unsigned long long q4 = q2 * q2;
                 p4lo += q4 & 0xFFFFFFFFull;
                 p4hi += q4 >> 32;
@@ -164,6 +169,10 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
                 }
     }
 
+    __syncthreads();
+    for (int i = tid; i < npair; i += bd)
+        atomicAdd(reinterpret_cast<unsigned long long *>(&g.PPacc[((size_t)(w * 64 + b) * g.K + j) * npair + i]),
+                  ppsh[i]);
     // block reduction: warp shuffles, one atomic per warp and quantity
     auto wsum = [](long long v) {
 #pragma unroll
@@ -197,8 +206,9 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
 
 size_t onetime_smem_bytes(const Group &g, int triples, int threads) {
     const int npair = g.R * (g.R - 1) / 2;
-    if (!triples || g.R < 3 || g.R > kMaxTripleR) return 0;
-    return (size_t)npair * (2 * g.L + 2) * threads;
+    const size_t pp = (size_t)npair * 8;
+    if (!triples || g.R < 3 || g.R > kMaxTripleR) return pp;
+    return pp + (size_t)npair * (2 * g.L + 2) * threads;
 }
 
 template <int L>

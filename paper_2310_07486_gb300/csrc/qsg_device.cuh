@@ -33,6 +33,7 @@ struct Group {
     unsigned long long *P4acc;  // [W*64][K][2] sum of Q_ab^4: low 32 bits and high bits summed apart
     long long *T3acc;         // [W*64][K] sum of Q_ab Q_bc Q_ca over slices and replica triples
     long long *Gacc, *F3acc;  // [W*64][K][L/2+1] momentum sums binned by x-distance
+    long long *PPacc;         // [W*64][K][R(R-1)/2] sum of Q_ab^2 of each replica pair
     double *outC, *outQ, *outP;
     double *outO;             // [W*64][K][7] one-time observables of every sample
     double *outK;             // [K][8] disorder averages

@@ -1,6 +1,7 @@
 // qsg_launch.h -- host-side launchers of the sm_103a kernels (internal).
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "qsg_device.cuh"
@@ -68,5 +69,19 @@ cudaError_t launch_finish(const Group &g, long long n_meas, cudaStream_t st);
 
 // Scratch words the correlator path needs for one (w, j) pair of the group.
 size_t measure_scratch_words_per_pair(const Group &g);
+
+// The 64 coupling features of every sample bit of the group, out [W*64][64].
+cudaError_t launch_features(const Group &g, float *out, cudaStream_t st);
+
+// Learned-ladder MLP (k_mlp.cu).  P: FP32 parameters, M, V: Adam moments;
+// one step = gradient of the batch idx[0..batch) (tiles of 16 samples into
+// `partial`), then Adam at step number t if adam != 0; grad_out and loss_out
+// (device) may be null.
+int mlp_param_count();
+cudaError_t launch_mlp_step(float *P, float *M, float *V, const float *X, const float *T, const int *idx, int batch,
+                            float *partial, float *loss_partial, float *grad_out, int adam, float lr, int t,
+                            float *loss_out, cudaStream_t st);
+cudaError_t launch_mlp_infer(const float *P, __nv_bfloat16 *Pb, const float *X, float *Y, long long n, int bf16,
+                             cudaStream_t st);
 
 }  // namespace qsg

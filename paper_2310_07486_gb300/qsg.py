@@ -75,6 +75,31 @@ def load_library(path: str | None = None):
     lib.qsg_read_onetime.argtypes = [vp, i32, vp, vp, vp]
     lib.qsg_read_onetime.restype = i32
     lib.qsg_read_energies.argtypes = [vp, i32, vp]
+    lib.qsg_read_pair_overlaps.restype = i32
+    lib.qsg_read_pair_overlaps.argtypes = [vp, i32, vp]
+    lib.qsg_sample_features.restype = i32
+    lib.qsg_sample_features.argtypes = [vp, i32, vp]
+    lib.qsg_mlp_param_count.restype = i32
+    lib.qsg_mlp_param_count.argtypes = []
+    lib.qsg_mlp_workspace_bytes.restype = sz
+    lib.qsg_mlp_workspace_bytes.argtypes = [ctypes.c_int64, i32]
+    lib.qsg_mlp_create.restype = i32
+    lib.qsg_mlp_create.argtypes = [ctypes.POINTER(vp), vp, sz, ctypes.c_int64, i32, vp]
+    lib.qsg_mlp_destroy.restype = None
+    lib.qsg_mlp_destroy.argtypes = [vp]
+    for name in ("qsg_mlp_set_params", "qsg_mlp_get_params"):
+        getattr(lib, name).restype = i32
+        getattr(lib, name).argtypes = [vp, vp]
+    lib.qsg_mlp_set_data.restype = i32
+    lib.qsg_mlp_set_data.argtypes = [vp, vp, vp, ctypes.c_int64]
+    lib.qsg_mlp_grad.restype = i32
+    lib.qsg_mlp_grad.argtypes = [vp, vp, i32, vp, vp]
+    lib.qsg_mlp_train.restype = i32
+    lib.qsg_mlp_train.argtypes = [vp, vp, i32, i32, ctypes.c_float, vp]
+    lib.qsg_mlp_predict.restype = i32
+    lib.qsg_mlp_predict.argtypes = [vp, vp, ctypes.c_int64, i32, vp]
+    lib.qsg_judge.restype = i32
+    lib.qsg_judge.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, vp]
     lib.qsg_fit_correlators.restype = i32
     lib.qsg_fit_correlators.argtypes = [vp, vp, i32, ctypes.c_int64, i32, i32, vp]
     lib.qsg_tau_tilde.restype = None
@@ -268,6 +293,18 @@ class Context:
         out["raw"] = raw
         return out
 
+    def qsg_read_pair_overlaps(self, group=0):
+        s = self.shapes[group]
+        out = np.zeros((s.n_samples, s.n_k, s.n_replicas * (s.n_replicas - 1) // 2), dtype=np.int64)
+        self._check(self.lib.qsg_read_pair_overlaps(self.h, group, _ptr(out)), "qsg_read_pair_overlaps")
+        return out
+
+    def qsg_sample_features(self, group=0):
+        s = self.shapes[group]
+        out = np.zeros((s.n_samples, 64), dtype=np.float32)
+        self._check(self.lib.qsg_sample_features(self.h, group, _ptr(out)), "qsg_sample_features")
+        return out
+
     def qsg_read_energies(self, group=0):
         s = self.shapes[group]
         E = np.zeros((s.n_samples, s.n_replicas, s.n_k), dtype=np.int64)
@@ -302,6 +339,94 @@ class Context:
 
     def qsg_set_counters(self, sweeps, swaps, n_meas=-1):
         self._check(self.lib.qsg_set_counters(self.h, int(sweeps), int(swaps), int(n_meas)), "qsg_set_counters")
+
+
+class MLP:
+    """A qsg_mlp over a torch-allocated device workspace; methods map onto
+    the qsg_mlp_* entry points."""
+
+    def __init__(self, n_data, max_batch, device=None, stream=None):
+        import torch
+        self.lib = load_library()
+        nbytes = int(self.lib.qsg_mlp_workspace_bytes(int(n_data), int(max_batch)))
+        if nbytes == 0:
+            raise QSGError(-1, "qsg_mlp_workspace_bytes")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        st = self.lib.qsg_mlp_create(ctypes.byref(h), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                     int(n_data), int(max_batch), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != 0:
+            raise QSGError(st, "qsg_mlp_create")
+        self.h = h
+        self.n_params = int(self.lib.qsg_mlp_param_count())
+
+    def _check(self, st, what):
+        if st != 0:
+            raise QSGError(st, what)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qsg_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        theta = np.ascontiguousarray(theta, dtype=np.float32)
+        assert theta.size == self.n_params
+        self._check(self.lib.qsg_mlp_set_params(self.h, _ptr(theta)), "qsg_mlp_set_params")
+
+    def get_params(self):
+        out = np.zeros(self.n_params, dtype=np.float32)
+        self._check(self.lib.qsg_mlp_get_params(self.h, _ptr(out)), "qsg_mlp_get_params")
+        return out
+
+    def set_data(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        self._keep = (X, T)
+        self._check(self.lib.qsg_mlp_set_data(self.h, _ptr(X), _ptr(T), X.shape[0]), "qsg_mlp_set_data")
+
+    def grad(self, idx):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        self._check(self.lib.qsg_mlp_grad(self.h, _ptr(idx), idx.size, ctypes.byref(loss), _ptr(g)), "qsg_mlp_grad")
+        return float(loss.value), g
+
+    def train(self, idx, lr):
+        idx = np.ascontiguousarray(idx, dtype=np.int32)
+        steps, batch = idx.shape
+        losses = np.zeros(steps, dtype=np.float32)
+        self._check(self.lib.qsg_mlp_train(self.h, _ptr(idx), steps, batch, float(lr), _ptr(losses)),
+                    "qsg_mlp_train")
+        return losses
+
+    def predict(self, X, bf16=True):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.zeros((X.shape[0], 33), dtype=np.float32)
+        self._check(self.lib.qsg_mlp_predict(self.h, _ptr(X), X.shape[0], 1 if bf16 else 0, _ptr(Y)),
+                    "qsg_mlp_predict")
+        return Y
+
+
+def qsg_judge(E_bins, q_bins, n_last=3):
+    """First passing bin per sample (-1 if none); E_bins [nb][ns][R][K],
+    q_bins [nb][ns][K][pairs]."""
+    E = np.ascontiguousarray(E_bins, dtype=np.float64)
+    q = np.ascontiguousarray(q_bins, dtype=np.float64)
+    nb, ns, R, K = E.shape
+    out = np.zeros(ns, dtype=np.int32)
+    st = load_library().qsg_judge(_ptr(E), _ptr(q), nb, ns, R, K, q.shape[3], int(n_last), _ptr(out))
+    if st != 0:
+        raise QSGError(st, "qsg_judge")
+    return out
 
 
 class qsg_fit_result(ctypes.Structure):

@@ -115,8 +115,9 @@ def test_bf16_rounding_matches_torch():
 
 
 def test_judge_on_a_geometric_drift():
-    """Bin means E_m = -1 - 0.5 * 2^-m with replica standard error 0.01 (and a
-    flat q^2): the first bin m with 0.5 (2^-(m-2) - 2^-m) <= sqrt(2) * 0.01 passes."""
+    """Bin means E_m = -1 - 0.5 * 2^-m at every k with replica standard error
+    0.01 (and a flat q^2): the first bin m with 0.5 (2^-(m-2) - 2^-m) <=
+    sqrt(2) * 0.01 passes."""
     nb, R, K, P = 12, 4, 2, 6
     E = np.zeros((nb, 1, R, K))
     q = np.full((nb, 1, K, P), 0.3)
