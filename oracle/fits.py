@@ -31,7 +31,10 @@ its R replicas at lags 0 .. L_tau/2:
      chi2/dof < 0.5; the one of the two with the smaller chi2/dof is kept and
      eta_e is its largest eta.
 Lags with sigma = 0 (tau = 0, where C = Q2 = 1 exactly) carry no weight and
-are left out of every fit.
+are left out of every fit.  A decay length beyond L_tau cannot be estimated
+(the paper says so of samples whose window reaches L_tau/2): the minimiser
+keeps every decay length in (0, 10 L_tau], and a fit that ends above L_tau
+marks its correlator (or its one- or two-term model) as not estimated.
 """
 from __future__ import annotations
 
@@ -161,16 +164,18 @@ def fit_C(C, s, Ltau, zeta):
         if dof < 1:
             return out
         B0, eta0 = _loglin_guess(tau.astype(float), C[tau])
-        p, err, chi2 = _lsq(model, jac, np.array([B0, eta0]), tau.astype(float), C[tau], s[tau],
-                            lambda q: q[1] > 0)
-        if p[1] > 0 and chi2 / dof < C_CHI2:
+        p, err, chi2 = _lsq(model, jac, np.array([B0, min(eta0, 10.0 * Ltau)]), tau.astype(float), C[tau], s[tau],
+                            lambda q: 0 < q[1] <= 10.0 * Ltau)
+        if chi2 / dof < C_CHI2:
+            if p[1] > Ltau:
+                return out  # eta beyond L_tau: not estimated
             out.update(ok=True, eta=float(p[1]), eta_err=float(err[1]), B=float(p[0]), chi2dof=chi2 / dof,
                        tau_min=int(tmin))
             return out
         tmin += 1
 
 
-def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl):
+def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl, Ltau):
     """Q2 = Q_pl + sum of nexp exponentials, tau_min from 1 up until
     chi2/dof < 0.5; returns (chi2/dof, params, errors, tau_min) or None."""
     def split(p):
@@ -206,9 +211,13 @@ def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl):
             q0 = [0.5 * B0, 2.0 * eta0, 0.5 * B0, 0.5 * eta0]
         p0 = np.array(([base] if free_pl else []) + q0)
         off = 1 if free_pl else 0
-        p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau], lambda q: bool(np.all(q[off + 1::2] > 0)))
+        p0[off + 1::2] = np.minimum(p0[off + 1::2], 10.0 * Ltau)
+        p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau],
+                            lambda q: bool(np.all((q[off + 1::2] > 0) & (q[off + 1::2] <= 10.0 * Ltau))))
         etas = p[off + 1::2]
-        if np.all(etas > 0) and chi2 / dof < Q_CHI2:
+        if chi2 / dof < Q_CHI2:
+            if np.any(etas > Ltau):
+                return None  # a decay length beyond L_tau: this model is not estimated
             return chi2 / dof, p, err, int(tmin)
     return None
 
@@ -225,7 +234,7 @@ def fit_Q2(Q, s, Ltau):
                eta_e=np.nan, eta_e_err=np.nan, eta_2=np.nan, chi2dof=np.nan, tau_min=0)
     best = None
     for nexp in (1, 2):
-        r = _fit_Q_terms(Q, s, tw, tw, nexp, qpl, free_pl=not pl_ok)
+        r = _fit_Q_terms(Q, s, tw, tw, nexp, qpl, free_pl=not pl_ok, Ltau=Ltau)
         if r is not None and (best is None or r[0] < best[1][0]):
             best = (nexp, r)
     if best is None:

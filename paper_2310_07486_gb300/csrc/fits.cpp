@@ -16,6 +16,9 @@
 //      exponentials on [tau_min, tau_w,Q2], tau_min from 1 up until
 //      chi2/dof < 0.5; the smaller chi2/dof is kept, eta_e = its largest eta.
 // Lags with sigma = 0 (tau = 0, where C = Q2 = 1 exactly) carry no weight.
+// A decay length beyond L_tau cannot be estimated: the minimiser keeps every
+// decay length in (0, 10 L_tau], and a fit ending above L_tau marks its
+// correlator (or its one- or two-term model) as not estimated.
 // The minimiser is Levenberg-Marquardt with analytic derivatives; the
 // parameter errors are the square roots of the diagonal of (J^T W J)^-1.
 #include <cmath>
@@ -32,6 +35,7 @@ constexpr int kMaxPar = 5;
 // Model: value and derivatives with respect to the parameters at lag t.
 struct Model {
     int np = 0;
+    double eta_max = INFINITY;  // decay lengths stay in (0, eta_max]
     virtual void eval(const double *p, double t, double *f, double *df) const = 0;
     virtual bool valid(const double *p) const = 0;  // decay lengths positive
     virtual ~Model() = default;
@@ -40,14 +44,17 @@ struct Model {
 // B [e^{-t/eta} + z e^{-(Lt - t)/eta}], p = (B, eta)
 struct CModel : Model {
     double Lt, z;
-    CModel(double Lt_, double z_) : Lt(Lt_), z(z_) { np = 2; }
+    CModel(double Lt_, double z_) : Lt(Lt_), z(z_) {
+        np = 2;
+        eta_max = 10.0 * Lt_;
+    }
     void eval(const double *p, double t, double *f, double *df) const override {
         const double e1 = std::exp(-t / p[1]), e2 = std::exp(-(Lt - t) / p[1]);
         *f = p[0] * (e1 + z * e2);
         df[0] = e1 + z * e2;
         df[1] = p[0] * (e1 * t + z * e2 * (Lt - t)) / (p[1] * p[1]);
     }
-    bool valid(const double *p) const override { return p[1] > 0.0; }
+    bool valid(const double *p) const override { return p[1] > 0.0 && p[1] <= eta_max; }
 };
 
 // Q_pl + sum_i B_i e^{-t/eta_i}; p = ([Q_pl,] B_1, eta_1, [B_2, eta_2])
@@ -55,8 +62,9 @@ struct QModel : Model {
     int nexp;
     bool free_pl;
     double qpl;
-    QModel(int nexp_, bool free_pl_, double qpl_) : nexp(nexp_), free_pl(free_pl_), qpl(qpl_) {
+    QModel(int nexp_, bool free_pl_, double qpl_, double eta_max_) : nexp(nexp_), free_pl(free_pl_), qpl(qpl_) {
         np = 2 * nexp + (free_pl ? 1 : 0);
+        eta_max = eta_max_;
     }
     void eval(const double *p, double t, double *f, double *df) const override {
         int o = 0;
@@ -77,7 +85,7 @@ struct QModel : Model {
     bool valid(const double *p) const override {
         const int o = free_pl ? 1 : 0;
         for (int i = 0; i < nexp; ++i)
-            if (!(p[o + 2 * i + 1] > 0.0)) return false;
+            if (!(p[o + 2 * i + 1] > 0.0 && p[o + 2 * i + 1] <= eta_max)) return false;
         return true;
     }
 };
@@ -239,8 +247,10 @@ void fit_C(const double *C, const double *s, int Lt, double z, qsg_fit_result *o
         if (dof < 1) return;
         double p[2], e[2];
         loglin_guess(d, &p[0], &p[1]);
+        p[1] = std::fmin(p[1], m.eta_max);
         const double c2 = levmar(m, d, p, e);
-        if (p[1] > 0.0 && c2 / dof < kChi2C) {
+        if (c2 / dof < kChi2C) {
+            if (p[1] > (double)Lt) return;  // eta beyond L_tau: not estimated
             o->C_ok = 1;
             o->C_tau_min = tmin;
             o->eta = p[1];
@@ -258,9 +268,9 @@ struct QFit {
     int tmin = 0;
 };
 
-QFit fit_Q_terms(const double *Q, const double *s, int tw, int nexp, double qpl, bool free_pl) {
+QFit fit_Q_terms(const double *Q, const double *s, int tw, int nexp, double qpl, bool free_pl, int Lt) {
     QFit r;
-    QModel m(nexp, free_pl, qpl);
+    QModel m(nexp, free_pl, qpl, 10.0 * Lt);
     for (int tmin = 1; tmin <= tw; ++tmin) {
         Data d = gather(Q, s, tmin, tw);
         const int dof = (int)d.t.size() - m.np;
@@ -282,8 +292,11 @@ QFit fit_Q_terms(const double *Q, const double *s, int tw, int nexp, double qpl,
             p[o + 2] = 0.5 * B0;
             p[o + 3] = 0.5 * eta0;
         }
+        for (int i = 0; i < nexp; ++i) p[o + 2 * i + 1] = std::fmin(p[o + 2 * i + 1], m.eta_max);
         const double c2 = levmar(m, d, p, e);
-        if (m.valid(p) && c2 / dof < kChi2Q) {
+        if (c2 / dof < kChi2Q) {
+            for (int i = 0; i < nexp; ++i)
+                if (p[o + 2 * i + 1] > (double)Lt) return r;  // beyond L_tau: not estimated
             r.ok = true;
             r.chi2dof = c2 / dof;
             r.tmin = tmin;
@@ -329,7 +342,7 @@ void fit_Q(const double *Q, const double *s, int Lt, qsg_fit_result *o) {
     QFit best;
     int best_n = 0;
     for (int nexp = 1; nexp <= 2; ++nexp) {
-        QFit r = fit_Q_terms(Q, s, tw, nexp, qpl, free_pl);
+        QFit r = fit_Q_terms(Q, s, tw, nexp, qpl, free_pl, Lt);
         if (r.ok && (!best.ok || r.chi2dof < best.chi2dof)) {
             best = r;
             best_n = nexp;
