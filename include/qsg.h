@@ -262,14 +262,17 @@ qsg_status qsg_mlp_predict(qsg_mlp *mlp, const float *X, int64_t n, int32_t bf16
 
 /* Log-binning thermalisation judge (host FP64).  Bins of sweeps
  * [2^m, 2^(m+1)); E_bins [n_bins][n_samples][n_replicas][n_k]: per replica,
- * the bin mean of the energy per site; q_bins [n_bins][n_samples][n_k][n_pairs]:
- * per replica pair, the bin mean of q^2.  Each replica's (pair's) values are
- * averaged over the k values; first_pass[b] (host int32 [n_samples]) = the
- * first bin m >= n_last - 1 such that each of bins m-1 .. m-n_last+1 agrees
- * with bin m within one combined standard error (over replicas for E, over
- * pairs for q^2), or -1.  n_replicas, n_pairs, n_last >= 2. */
+ * the bin mean of the energy per site; q_bins [n_bins][n_samples][n_k][pairs]:
+ * per replica pair ((0,1), (0,2), ..., (R-2,R-1), as qsg_read_pair_overlaps),
+ * the bin mean of q^2.  Each replica's (pair's) values are averaged over the
+ * k values.  Energy: mean over replicas with the standard error of their
+ * spread; q^2: mean over pairs with the jackknife standard error over
+ * replicas.  first_pass[b] (host int32 [n_samples]) = the first bin
+ * m >= n_last - 1 such that each of bins m-1 .. m-n_last+1 agrees with bin m
+ * within n_sigma combined standard errors for both, or -1.
+ * n_replicas >= 3, n_last >= 2, n_sigma > 0. */
 qsg_status qsg_judge(const double *E_bins, const double *q_bins, int32_t n_bins, int32_t n_samples,
-                     int32_t n_replicas, int32_t n_k, int32_t n_pairs, int32_t n_last, int32_t *first_pass);
+                     int32_t n_replicas, int32_t n_k, int32_t n_last, double n_sigma, int32_t *first_pass);
 
 /* Action E of every configuration, host int64 [n_samples][R][K] (ladder
  * position j).  Computes it if no sweep fused it.  Synchronises the stream. */

@@ -209,36 +209,41 @@ def ladder_from_output(y, k_min, k_max):
 # --------------------------------------------------------------------------
 # log-binning judge
 # --------------------------------------------------------------------------
-def judge(E_bins, q_bins, n_last=3):
+def judge(E_bins, q_bins, n_last=3, n_sigma=2.0):
     """First bin at which a sample counts as thermalised, or -1.
 
     E_bins [n_bins][n_samples][R][K]: per replica, the mean energy per site over
     the tempering steps of bin m (sweeps in [2^m, 2^(m+1))).
-    q_bins [n_bins][n_samples][K][n_pairs]: per replica pair, the mean q^2 of
-    the measurements of bin m.
-    Each replica's (pair's) bin means are averaged over the K ladder points;
-    bin m passes when each of the bins m-1 .. m-n_last+1 agrees with it within
-    one combined standard error (sqrt(se_m^2 + se_i^2), se over replicas for
-    the energy and over pairs for q^2)."""
+    q_bins [n_bins][n_samples][K][n_pairs]: per replica pair (pairs in the order
+    (0,1), (0,2), ..., (R-2,R-1)), the mean q^2 of the measurements of bin m.
+    Each replica's (pair's) bin means are averaged over the K ladder points.
+    Energy: mean over replicas, standard error from the replica spread.  q^2:
+    mean over pairs, standard error by the jackknife over replicas (leaving
+    out replica r drops the pairs that contain it), since pairs that share a
+    replica are not independent.  Bin m passes when each of the bins
+    m-1 .. m-n_last+1 agrees with it within n_sigma combined standard errors
+    (n_sigma sqrt(se_m^2 + se_i^2)) for both observables."""
     E_bins = np.asarray(E_bins, dtype=np.float64)
     q_bins = np.asarray(q_bins, dtype=np.float64)
-    nb, ns = E_bins.shape[0], E_bins.shape[1]
+    nb, ns, R = E_bins.shape[0], E_bins.shape[1], E_bins.shape[2]
+    pairs = [(a, b) for a in range(R) for b in range(a + 1, R)]
     out = np.full(ns, -1, dtype=np.int64)
 
-    def stats(a):  # mean and standard error over the last axis
-        n = a.shape[-1]
-        m = a.mean(axis=-1)
-        se = np.sqrt(((a - m[..., None]) ** 2).sum(axis=-1) / (n * (n - 1)))
-        return m, se
-
-    Em, Es = stats(E_bins.mean(axis=3))            # per replica, k-averaged: [nb][ns]
-    qm, qs = stats(q_bins.mean(axis=2))            # per pair, k-averaged: [nb][ns]
+    e = E_bins.mean(axis=3)                       # [nb][ns][R]
+    Em = e.mean(axis=2)
+    Es = np.sqrt(((e - Em[..., None]) ** 2).sum(axis=2) / (R * (R - 1)))
+    q = q_bins.mean(axis=2)                       # [nb][ns][pairs]
+    qm = q.mean(axis=2)
+    jk = np.stack([q[:, :, [i for i, (a, b) in enumerate(pairs) if r not in (a, b)]].mean(axis=2)
+                   for r in range(R)], axis=2)    # [nb][ns][R] leave-one-replica-out means
+    jm = jk.mean(axis=2)
+    qs = np.sqrt((R - 1) / R * ((jk - jm[..., None]) ** 2).sum(axis=2))
     for b in range(ns):
         for m in range(n_last - 1, nb):
             ok = True
             for i in range(1, n_last):
                 for mean, se in ((Em, Es), (qm, qs)):
-                    if abs(mean[m, b] - mean[m - i, b]) > np.sqrt(se[m, b] ** 2 + se[m - i, b] ** 2):
+                    if abs(mean[m, b] - mean[m - i, b]) > n_sigma * math.sqrt(se[m, b] ** 2 + se[m - i, b] ** 2):
                         ok = False
             if ok:
                 out[b] = m

@@ -4,10 +4,12 @@
 //
 // Bins of sweeps [2^m, 2^(m+1)).  For every sample, the bin mean of the
 // energy per site of each replica and of q^2 of each replica pair, averaged
-// over the ladder's k values; their mean over replicas (pairs) and its
-// standard error.  A sample is thermalised at the first bin m >= n_last - 1
-// that agrees with each of the n_last - 1 bins before it within one combined
-// standard error sqrt(se_m^2 + se_i^2), for both observables.
+// over the ladder's k values.  Energy: mean over replicas, standard error
+// from their spread.  q^2: mean over pairs, standard error by the jackknife
+// over replicas (leaving out replica r drops the pairs that contain it; pairs
+// sharing a replica are not independent).  A sample is thermalised at the
+// first bin m >= n_last - 1 that agrees with each of the n_last - 1 bins
+// before it within n_sigma combined standard errors, for both observables.
 #include <cmath>
 #include <vector>
 
@@ -15,43 +17,64 @@
 
 namespace {
 
-// k-averaged value of replica (pair) r: a[r * rs + k * ks], k < K
 double kavg(const double *a, int K, size_t ks) {
     double s = 0.0;
     for (int k = 0; k < K; ++k) s += a[(size_t)k * ks];
     return s / K;
 }
 
-void mean_se(const double *v, int n, double *mean, double *se) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += v[i];
-    const double m = s / n;
-    double var = 0.0;
-    for (int i = 0; i < n; ++i) var += (v[i] - m) * (v[i] - m);
-    *mean = m;
-    *se = std::sqrt(var / ((double)n * (n - 1)));
-}
-
 }  // namespace
 
 extern "C" qsg_status qsg_judge(const double *E_bins, const double *q_bins, int32_t n_bins, int32_t n_samples,
-                                int32_t n_replicas, int32_t n_k, int32_t n_pairs, int32_t n_last,
+                                int32_t n_replicas, int32_t n_k, int32_t n_last, double n_sigma,
                                 int32_t *first_pass) {
-    if (!E_bins || !q_bins || !first_pass || n_bins < 0 || n_samples < 0 || n_replicas < 2 || n_k < 1 ||
-        n_pairs < 2 || n_last < 2)
+    if (!E_bins || !q_bins || !first_pass || n_bins < 0 || n_samples < 0 || n_replicas < 3 || n_k < 1 ||
+        n_last < 2 || !(n_sigma > 0.0))
         return QSG_ERR_ARG;
-    const int R = n_replicas, K = n_k, P = n_pairs;
-    // per bin and sample: mean and standard error of the k-averaged E (over
-    // replicas) and q^2 (over pairs)
+    const int R = n_replicas, K = n_k, P = R * (R - 1) / 2;
+    std::vector<int> pa(P), pb(P);
+    for (int a = 0, i = 0; a < R; ++a)
+        for (int b = a + 1; b < R; ++b, ++i) {
+            pa[i] = a;
+            pb[i] = b;
+        }
     std::vector<double> Em((size_t)n_bins * n_samples), Es(Em.size()), qm(Em.size()), qs(Em.size());
-    std::vector<double> tmp(R > P ? R : P);
+    std::vector<double> e(R), q(P), jk(R);
     for (int m = 0; m < n_bins; ++m)
         for (int b = 0; b < n_samples; ++b) {
             const size_t c = (size_t)m * n_samples + b;
-            for (int r = 0; r < R; ++r) tmp[r] = kavg(E_bins + (c * R + r) * K, K, 1);
-            mean_se(tmp.data(), R, &Em[c], &Es[c]);
-            for (int p = 0; p < P; ++p) tmp[p] = kavg(q_bins + c * K * P + p, K, (size_t)P);
-            mean_se(tmp.data(), P, &qm[c], &qs[c]);
+            double s = 0.0;
+            for (int r = 0; r < R; ++r) {
+                e[r] = kavg(E_bins + (c * R + r) * K, K, 1);
+                s += e[r];
+            }
+            const double mean = s / R;
+            double v = 0.0;
+            for (int r = 0; r < R; ++r) v += (e[r] - mean) * (e[r] - mean);
+            Em[c] = mean;
+            Es[c] = std::sqrt(v / ((double)R * (R - 1)));
+            double qsum = 0.0;
+            for (int p = 0; p < P; ++p) {
+                q[p] = kavg(q_bins + c * K * P + p, K, (size_t)P);
+                qsum += q[p];
+            }
+            qm[c] = qsum / P;
+            double jsum = 0.0;
+            for (int r = 0; r < R; ++r) {
+                double t = 0.0;
+                int n = 0;
+                for (int p = 0; p < P; ++p)
+                    if (pa[p] != r && pb[p] != r) {
+                        t += q[p];
+                        ++n;
+                    }
+                jk[r] = t / n;
+                jsum += jk[r];
+            }
+            const double jm = jsum / R;
+            double jv = 0.0;
+            for (int r = 0; r < R; ++r) jv += (jk[r] - jm) * (jk[r] - jm);
+            qs[c] = std::sqrt((double)(R - 1) / R * jv);
         }
     for (int b = 0; b < n_samples; ++b) {
         first_pass[b] = -1;
@@ -60,8 +83,8 @@ extern "C" qsg_status qsg_judge(const double *E_bins, const double *q_bins, int3
             const size_t c = (size_t)m * n_samples + b;
             for (int i = 1; i < n_last; ++i) {
                 const size_t d = (size_t)(m - i) * n_samples + b;
-                if (std::fabs(Em[c] - Em[d]) > std::sqrt(Es[c] * Es[c] + Es[d] * Es[d])) ok = false;
-                if (std::fabs(qm[c] - qm[d]) > std::sqrt(qs[c] * qs[c] + qs[d] * qs[d])) ok = false;
+                if (std::fabs(Em[c] - Em[d]) > n_sigma * std::sqrt(Es[c] * Es[c] + Es[d] * Es[d])) ok = false;
+                if (std::fabs(qm[c] - qm[d]) > n_sigma * std::sqrt(qs[c] * qs[c] + qs[d] * qs[d])) ok = false;
             }
             if (ok) first_pass[b] = m;
         }

@@ -99,7 +99,7 @@ def load_library(path: str | None = None):
     lib.qsg_mlp_predict.restype = i32
     lib.qsg_mlp_predict.argtypes = [vp, vp, ctypes.c_int64, i32, vp]
     lib.qsg_judge.restype = i32
-    lib.qsg_judge.argtypes = [vp, vp, i32, i32, i32, i32, i32, i32, vp]
+    lib.qsg_judge.argtypes = [vp, vp, i32, i32, i32, i32, i32, ctypes.c_double, vp]
     lib.qsg_fit_correlators.restype = i32
     lib.qsg_fit_correlators.argtypes = [vp, vp, i32, ctypes.c_int64, i32, i32, vp]
     lib.qsg_tau_tilde.restype = None
@@ -416,14 +416,15 @@ class MLP:
         return Y
 
 
-def qsg_judge(E_bins, q_bins, n_last=3):
+def qsg_judge(E_bins, q_bins, n_last=3, n_sigma=2.0):
     """First passing bin per sample (-1 if none); E_bins [nb][ns][R][K],
     q_bins [nb][ns][K][pairs]."""
     E = np.ascontiguousarray(E_bins, dtype=np.float64)
     q = np.ascontiguousarray(q_bins, dtype=np.float64)
     nb, ns, R, K = E.shape
+    assert q.shape == (nb, ns, K, R * (R - 1) // 2)
     out = np.zeros(ns, dtype=np.int32)
-    st = load_library().qsg_judge(_ptr(E), _ptr(q), nb, ns, R, K, q.shape[3], int(n_last), _ptr(out))
+    st = load_library().qsg_judge(_ptr(E), _ptr(q), nb, ns, R, K, int(n_last), float(n_sigma), _ptr(out))
     if st != 0:
         raise QSGError(st, "qsg_judge")
     return out

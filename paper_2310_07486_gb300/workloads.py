@@ -74,3 +74,32 @@ def ragged() -> Workload:
 
 
 ALL = {w().name: w for w in (smallest, mid_scale, largest, ragged)}
+
+
+def bimodal_couplings(n: int, L: int, seed: int) -> np.ndarray:
+    """n samples of J = +-1 with probability 1/2 on the 2 L^2 bonds (the
+    paper's bimodal disorder), as host int8 [n][2][L][L] for
+    qsg_set_couplings; drawn from numpy's seeded generator."""
+    rng = np.random.default_rng(seed)
+    return (1 - 2 * rng.integers(0, 2, size=(n, 2, L, L))).astype(np.int8)
+
+
+@dataclass
+class LadderStudy:
+    """Sizes of the learned-ladder study (scaled down from 2000 training runs
+    at L = 12..20 and 256 evaluation samples at L = 24, L_tau = 2048)."""
+    train_sizes: list = field(default_factory=lambda: [(4, 16), (6, 32)])
+    n_train_per_size: int = 1024
+    eval_size: tuple = (8, 32)
+    n_eval: int = 256
+    k_min: float = 0.2
+    k_max: float = 0.45
+    n_k: int = 32
+    replicas: int = 4
+    sweeps_per_swap: int = 8
+    max_bin: int = 13          # bins of sweeps [2^m, 2^(m+1)), m < max_bin
+    seed: int = 2024
+
+
+def ladder_study() -> LadderStudy:
+    return LadderStudy()

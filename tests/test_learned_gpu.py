@@ -130,7 +130,7 @@ def test_mlp_inference_matches_oracle(bf16):
 
 def test_judge_matches_oracle():
     rng = np.random.default_rng(3)
-    nb, ns, R, K, P = 10, 40, 4, 3, 6
+    nb, ns, R, K, P = 10, 40, 4, 3, 6  # P = R (R - 1) / 2
     drift = (2.0 ** -np.arange(nb))[:, None, None, None] * rng.uniform(0, 0.2, size=(1, ns, 1, K))
     E = -1 - drift + rng.normal(scale=0.01, size=(nb, ns, R, K))
     q = 0.3 + drift[:, :, 0, :][..., None] + rng.normal(scale=0.01, size=(nb, ns, K, P))

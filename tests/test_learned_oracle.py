@@ -117,21 +117,46 @@ def test_bf16_rounding_matches_torch():
 def test_judge_on_a_geometric_drift():
     """Bin means E_m = -1 - 0.5 * 2^-m at every k with replica standard error
     0.01 (and a flat q^2): the first bin m with 0.5 (2^-(m-2) - 2^-m) <=
-    sqrt(2) * 0.01 passes."""
-    nb, R, K, P = 12, 4, 2, 6
+    2 sqrt(2) * 0.01 passes (two combined standard errors)."""
+    nb, R, K = 12, 4, 2
+    P = R * (R - 1) // 2
     E = np.zeros((nb, 1, R, K))
     q = np.full((nb, 1, K, P), 0.3)
-    q += np.array([-1, 1, -1, 1, -1, 1]) * 0.001
-    spread = 0.01 * math.sqrt(R) * math.sqrt((R - 1) / R)  # so that the standard error is 0.01
+    spread = 0.01 * math.sqrt(R - 1)  # so that the standard error over replicas is 0.01
     dev = np.array([-1, 1, -1, 1]) * spread
     for m in range(nb):
         E[m, 0, :, :] = (-1 - 0.5 * 2.0 ** -m) + dev[:, None]
-    want = next(m for m in range(2, nb) if 0.5 * (2.0 ** -(m - 2) - 2.0 ** -m) <= math.sqrt(2) * 0.01)
+    want = next(m for m in range(2, nb) if 0.5 * (2.0 ** -(m - 2) - 2.0 ** -m) <= 2 * math.sqrt(2) * 0.01)
     assert OL.judge(E, q)[0] == want
 
 
+def test_judge_jackknife_error_of_q2_over_replicas():
+    """q^2 of pair (a, b) = u_a + u_b: leaving replica r out, the pair mean
+    moves by a known amount; the jackknife error of the mean over pairs is
+    then sqrt((R-1)/R sum_r (J_r - mean J)^2) with J_r the mean over pairs
+    without r.  A drift of the q^2 mean by exactly 2.001 of those combined
+    errors fails, 1.999 passes."""
+    R, K = 4, 1
+    u = np.array([0.0, 0.01, 0.03, 0.02])
+    pairs = [(a, b) for a in range(R) for b in range(a + 1, R)]
+    base = np.array([u[a] + u[b] for a, b in pairs])
+    Jr = np.array([np.mean([base[i] for i, (a, b) in enumerate(pairs) if r not in (a, b)]) for r in range(R)])
+    se = math.sqrt((R - 1) / R * ((Jr - Jr.mean()) ** 2).sum())
+    for factor, want in ((1.999, 2), (2.001, 3)):
+        step = factor * math.sqrt(2) * se
+        nb = 4
+        E = np.zeros((nb, 1, R, K)) + np.array([-1, 1, -1, 1])[None, None, :, None] * 1e-3
+        q = np.zeros((nb, 1, K, len(pairs)))
+        q[0, 0, 0] = base
+        q[1, 0, 0] = base + step        # bins 1, 2, 3 agree; bin 0 is one step below
+        q[2, 0, 0] = base + step
+        q[3, 0, 0] = base + step
+        assert OL.judge(E, q)[0] == want, factor
+
+
 def test_judge_never_passes_a_steady_trend():
-    nb, R, K, P = 10, 4, 1, 6
+    nb, R, K = 10, 4, 1
+    P = R * (R - 1) // 2
     E = np.zeros((nb, 1, R, K))
     for m in range(nb):
         E[m] = -m + np.array([-1, 1, -1, 1])[:, None] * 0.01
