@@ -82,7 +82,7 @@ typedef struct {
     int32_t L;          /* linear size, even, 2 <= L <= 32 */
     int32_t Ltau;       /* Trotter slices, even, 2 <= L_tau <= 65536 */
     int32_t n_samples;  /* disorder samples, >= 1 (stored in ceil(n/64) words) */
-    int32_t n_replicas; /* independent replicas per sample and k, >= 1 */
+    int32_t n_replicas; /* independent replicas per sample and k, 1 <= R <= 1023 */
     int32_t n_k;        /* ladder length K, 1 <= K <= 128 */
     int32_t algo;       /* QSG_METROPOLIS or QSG_HEATBATH */
     int32_t boundary;   /* QSG_PBC or QSG_APBC (along tau only; Methods, Trotter-Suzuki) */

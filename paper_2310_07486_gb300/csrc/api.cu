@@ -27,7 +27,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 bool valid_shape(const qsg_shape &s) {
     if (s.L < 2 || s.L > 32 || (s.L & 1)) return false;
     if (s.Ltau < 2 || s.Ltau > 65536 || (s.Ltau & 1)) return false;
-    if (s.n_samples < 1 || s.n_replicas < 1 || s.n_k < 1 || s.n_k > 128) return false;
+    if (s.n_samples < 1 || s.n_replicas < 1 || s.n_replicas > 1023 || s.n_k < 1 || s.n_k > 128) return false;
     if (s.algo != QSG_METROPOLIS && s.algo != QSG_HEATBATH) return false;
     if (s.boundary != QSG_PBC && s.boundary != QSG_APBC) return false;
     if (s.reserved != 0) return false;

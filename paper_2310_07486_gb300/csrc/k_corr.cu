@@ -93,6 +93,8 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
                            int *status, cudaStream_t st) {
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
+    // the tensor-core Gram launch puts (pair, replica, sample bit) on gridDim.y (<= 65535)
+    if (tensor && batch > 65535 / (g.R * 64)) batch = 65535 / (g.R * 64);
     if (batch < 1) return cudaErrorInvalidValue;
     const int npairs_total = g.W * g.K;
     const size_t sh_bytes = (size_t)g.Ltau * g.nwx * sizeof(uint64_t);

@@ -97,7 +97,7 @@ class LadderStudy:
     n_k: int = 32
     replicas: int = 4
     sweeps_per_swap: int = 8
-    max_bin: int = 13          # bins of sweeps [2^m, 2^(m+1)), m < max_bin
+    max_bin: int = 14          # bins of sweeps (2^m, 2^(m+1)], m < max_bin
     seed: int = 2024
 
 

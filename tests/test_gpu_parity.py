@@ -433,3 +433,24 @@ def test_onetime_without_triples_keeps_pair_sums():
     for f in ("q2", "q4", "chi2", "F2", "chi_lin"):
         assert np.array_equal(a[f], b[f])
     assert np.all(np.isnan(b["chi3"])) and np.all(np.isfinite(a["chi3"]))
+
+
+def test_many_ladder_pairs_in_one_measurement_batch():
+    """Short L_tau and many (word, k) pairs: the correlator batch is limited
+    by the launch grid, not by the scratch; sampled samples match the oracle."""
+    shape = Q.Shape(4, 16, 1024, 4, 32, Q.HEATBATH, Q.PBC)
+    lad = np.linspace(0.2, 0.45, 32)
+    ctx = Q.Context([shape])
+    ctx.qsg_init_samples(61, [lad])
+    ctx.qsg_sweep(3)
+    ctx.qsg_measure_correlators()
+    got = ctx.qsg_read_correlators(raw=True)
+    for b in (0, 517, 1023):
+        o = oracle.OracleGroup(4, 16, 1, 4, 32, algo="heatbath", first_sample=b)
+        o.init(61, lad)
+        o.sweep(3)
+        o.measure()
+        ref = o.read()
+        assert np.array_equal(got["C_raw"][:, b], ref["C_raw"][:, 0])
+        assert np.array_equal(got["Q2_raw"][:, b], ref["Q2_raw"][:, 0])
+        assert np.array_equal(got["q2_raw"][b], ref["q2_raw"][0])
