@@ -300,8 +300,10 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *   QSG_OPT_CHUNK         tau planes per wavefront work unit (0 = automatic;
  *                         otherwise a multiple of 8 that divides every L_tau)
  *   QSG_OPT_WAVEFRONT_VARIANT  register budget of the wavefront kernel:
- *                         0 = two blocks per SM, 1 = three blocks per SM;
- *                         process-wide
+ *                         0 = two blocks per SM with the couplings held in
+ *                         registers, 1 = three blocks per SM, 2 = two blocks
+ *                         per SM with the couplings re-read from shared
+ *                         memory; process-wide
  *   QSG_OPT_CORR_KERNEL   0 = tensor cores (Gram tiles by tcgen05.mma in FP8,
  *                         exact for +-1 spins), 1 = XOR/popcount on the
  *                         integer pipes

@@ -706,7 +706,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         return QSG_OK;
     }
     if (option == QSG_OPT_WAVEFRONT_VARIANT) {
-        if (value < 0 || value > 1) return QSG_ERR_ARG;
+        if (value < 0 || value > 2) return QSG_ERR_ARG;
         g_wavefront_variant = (int)value;
         return QSG_OK;
     }

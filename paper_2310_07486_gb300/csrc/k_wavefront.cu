@@ -25,6 +25,8 @@
 // thread is class "even" at index c = thread index, so the active sites of a
 // step and their neighbours are read by consecutive threads from consecutive
 // words.
+#include <type_traits>
+
 #include "qsg_launch.h"
 
 namespace qsg {
@@ -186,7 +188,7 @@ __device__ __forceinline__ void boundary_update(const Group &g, const Thr &t, ui
 // `ring` (kRing * SLOT + 2 L^2 words of shared memory); threads with
 // active == false only take part in the barriers.  do_boundary is one int of
 // shared memory for this unit.
-template <int ALGO, int SLOT>
+template <int ALGO, int SLOT, bool JREG = false>
 __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, const int nch, const int s, const int ch,
                                                const bool active, const int c, uint64_t *ring, int *do_boundary,
                                                const uint32_t sweep, const uint32_t k0, const uint32_t k1,
@@ -212,10 +214,13 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
     const uint32_t qstride = (uint32_t)(L * half);
     const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
 
-    // plane p of the chunk lives in ring slot (p - a + 1) & 15
-    auto issue_plane = [&](int p, uint64_t *dst) {
-        if (active && p <= b) {
-            const int gp = p < 0 ? p + Lt : (p >= Lt ? p - Lt : p);
+    // plane p of the chunk lives in ring slot (p - a + 1) & 15.  `edge` is false
+    // in the interior of the chunk, where every plane issued lies in [a, b)
+    // and needs no wrap.
+    auto issue_plane = [&](int p, uint64_t *dst, auto edge) {
+        constexpr bool E = decltype(edge)::value;
+        if (active && (!E || p <= b)) {
+            const int gp = !E ? p : (p < 0 ? p + Lt : (p >= Lt ? p - Lt : p));
             const uint64_t *src = Sg + (size_t)gp * L2 + 2 * c;
             cp_async8(dst + t.dA, src);
             cp_async8(dst + t.dB, src + 1);
@@ -227,7 +232,7 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
 
     // prologue: planes a-1 .. a+7 in slots 0 .. 8
 #pragma unroll
-    for (int i = 0; i < 9; ++i) issue_plane(a - 1 + i, ring + i * SLOT);
+    for (int i = 0; i < 9; ++i) issue_plane(a - 1 + i, ring + i * SLOT, std::true_type{});
     cp_commit();
     uint4 rcur = philox4x32_10(make_uint4((uint32_t)(a >> 1) * qstride + t.qrow, sweep, (uint32_t)s, tag), k0, k1);
     uint32_t carry = 0;
@@ -240,6 +245,18 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
     W0[7] = ring[0 * SLOT + t.o0];  // plane a-1
     W1[7] = ring[0 * SLOT + t.o1];
     W0[0] = ring[1 * SLOT + t.o0];  // plane a
+    // couplings of the thread's two sites (JREG: held in registers for the
+    // whole chunk instead of re-read from shared memory every super step)
+    uint64_t Jr0 = 0, Jl0 = 0, Ju0 = 0, Jd0 = 0, Jr1 = 0, Ju1 = 0, Jd1 = 0;
+    if (JREG) {
+        Jr0 = sJx[t.o0];
+        Jl0 = sJx[t.l0];
+        Ju0 = sJy[t.o0];
+        Jd0 = sJy[t.d0];
+        Jr1 = sJx[t.o1];
+        Ju1 = sJy[t.o1];
+        Jd1 = sJy[t.d1];
+    }
     W1[0] = ring[1 * SLOT + t.o1];
 
 // ring slot of plane a + p_rel; inside the loop p_rel is taken modulo 16
@@ -256,21 +273,23 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
         W0[RP2] = QSG_SLOT(Q + 2)[t.o0];                                                                          \
         W1[RP2] = QSG_SLOT(Q + 2)[t.o1];                                                                          \
         /* prefetch planes q+8, q+9 */                                                                            \
-        issue_plane(q + 8, QSG_SLOT(Q + 8));                                                                      \
-        issue_plane(q + 9, QSG_SLOT(Q + 9));                                                                      \
+        issue_plane(q + 8, QSG_SLOT(Q + 8), std::integral_constant<bool, EDGE>{});                                \
+        issue_plane(q + 9, QSG_SLOT(Q + 9), std::integral_constant<bool, EDGE>{});                                \
         cp_commit();                                                                                              \
-        const uint64_t jr0 = sJx[t.o0], jl0 = sJx[t.l0], ju0 = sJy[t.o0], jd0 = sJy[t.d0];                        \
-        const uint64_t jr1 = sJx[t.o1], ju1 = sJy[t.o1], jd1 = sJy[t.d1];                                         \
+        const uint64_t jr0 = JREG ? Jr0 : sJx[t.o0], jl0 = JREG ? Jl0 : sJx[t.l0];                                 \
+        const uint64_t ju0 = JREG ? Ju0 : sJy[t.o0], jd0 = JREG ? Jd0 : sJy[t.d0];                                 \
+        const uint64_t jr1 = JREG ? Jr1 : sJx[t.o1], ju1 = JREG ? Ju1 : sJy[t.o1], jd1 = JREG ? Jd1 : sJy[t.d1];   \
         const uint4 r = rcur;                                                                                     \
         if (active) {                                                                                             \
             /* colour 0 of plane q (column x0) and of plane q+1 (column x0+1) */                                  \
             uint64_t *pq = QSG_SLOT(Q);                                                                           \
             uint64_t *pq1 = QSG_SLOT(Q + 1);                                                                      \
             W0[R0] = update_site<ALGO>(W0[R0], W1[R0], pq[t.l0], pq[t.u0], pq[t.d0], W0[RP1],                     \
-                                       W0[RM1] ^ (q == 0 ? apbc : 0ull), jr0, jl0, ju0, jd0, r.x, T);             \
+                                       W0[RM1] ^ (EDGE && q == 0 ? apbc : 0ull), jr0, jl0, ju0, jd0, r.x, T);     \
             pq[t.o0] = W0[R0];                                                                                    \
             W1[RP1] = update_site<ALGO>(W1[RP1], pq1[t.r1], W0[RP1], pq1[t.u1], pq1[t.d1],                        \
-                                        W1[RP2] ^ (q + 1 == Lt - 1 ? apbc : 0ull), W1[R0], jr1, jr0, ju1, jd1,    \
+                                        W1[RP2] ^ (EDGE && q + 1 == Lt - 1 ? apbc : 0ull), W1[R0], jr1, jr0, ju1, \
+                                        jd1,                                                                      \
                                         r.w, T);                                                                  \
             pq1[t.o1] = W1[RP1];                                                                                  \
         }                                                                                                         \
@@ -280,7 +299,7 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
         rcur = philox4x32_10(make_uint4((uint32_t)((q + 2) >> 1) * qstride + t.qrow, sweep, (uint32_t)s, tag),    \
                              k0, k1);                                                                             \
         if (active) {                                                                                             \
-            if (q >= a + 2) {                                                                                     \
+            if (!EDGE || q >= a + 2) {                                                                            \
                 /* colour 1 of plane q-1 (column x0) and of plane q (column x0+1) */                              \
                 uint64_t *pm = QSG_SLOT(Q - 1);                                                                   \
                 uint64_t *pq = QSG_SLOT(Q);                                                                       \
@@ -292,21 +311,36 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
                 pq[t.o1] = W1[R0];                                                                                \
             }                                                                                                     \
             /* planes q-3 and q-2 became final in the previous super step */                                     \
-            if (q - 3 >= a) writeback(q - 3, QSG_SLOT(Q - 3));                                                    \
-            if (q - 2 >= a) writeback(q - 2, QSG_SLOT(Q - 2));                                                    \
+            if (!EDGE || q - 3 >= a) writeback(q - 3, QSG_SLOT(Q - 3));                                           \
+            if (!EDGE || q - 2 >= a) writeback(q - 2, QSG_SLOT(Q - 2));                                           \
         }                                                                                                         \
         carry = r.z;                                                                                              \
     }
 
+    // the first and last 16 planes of the chunk carry the boundary checks; the
+    // interior runs a copy of the same steps without them
     for (int base = a; base < b; base += 16) {
-        QSG_SUPER(0)
-        QSG_SUPER(1)
-        QSG_SUPER(2)
-        QSG_SUPER(3)
-        QSG_SUPER(4)
-        QSG_SUPER(5)
-        QSG_SUPER(6)
-        QSG_SUPER(7)
+        if (base == a || base + 16 >= b) {
+            constexpr bool EDGE = true;
+            QSG_SUPER(0)
+            QSG_SUPER(1)
+            QSG_SUPER(2)
+            QSG_SUPER(3)
+            QSG_SUPER(4)
+            QSG_SUPER(5)
+            QSG_SUPER(6)
+            QSG_SUPER(7)
+        } else {
+            constexpr bool EDGE = false;
+            QSG_SUPER(0)
+            QSG_SUPER(1)
+            QSG_SUPER(2)
+            QSG_SUPER(3)
+            QSG_SUPER(4)
+            QSG_SUPER(5)
+            QSG_SUPER(6)
+            QSG_SUPER(7)
+        }
     }
 #undef QSG_SUPER
 
@@ -343,7 +377,7 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
 }
 
 // One launch per sweep of one group: P units per block (blocks of P * L^2 / 2 threads).
-template <int ALGO, int SLOT, int NREG>
+template <int ALGO, int SLOT, int NREG, bool JREG = false>
 __global__ void __launch_bounds__(512) __maxnreg__(NREG)
     k_sweep_wavefront(const Group g, const int C, const int nch, const int P, const uint32_t *sweep_base,
                       const uint32_t sweep_off, const uint32_t k0, const uint32_t k1, unsigned *__restrict__ arrivals) {
@@ -358,7 +392,7 @@ __global__ void __launch_bounds__(512) __maxnreg__(NREG)
     const bool active = unit < g.nslots * nch;
     const int s = active ? unit / nch : 0;
     const int ch = active ? unit - s * nch : 0;
-    wavefront_unit<ALGO, SLOT>(g, C, nch, s, ch, active, c, smem + (size_t)u * (kRing * SLOT + 2 * L2),
+    wavefront_unit<ALGO, SLOT, JREG>(g, C, nch, s, ch, active, c, smem + (size_t)u * (kRing * SLOT + 2 * L2),
                                &do_boundary[u], sweep, k0, k1, arrivals);
 }
 
@@ -391,7 +425,7 @@ __global__ void __launch_bounds__(288) __maxnreg__(NREG)
         const int lu = unit - prefix[k];
         const int s = lu / nch, ch = lu - s * nch;
         const bool active = (int)threadIdx.x < g.L * g.L / 2;
-        wavefront_unit<ALGO, SLOT>(g, C, nch, s, ch, active, active ? (int)threadIdx.x : 0, smem, &do_boundary, sweep,
+        wavefront_unit<ALGO, SLOT, true>(g, C, nch, s, ch, active, active ? (int)threadIdx.x : 0, smem, &do_boundary, sweep,
                                    k0, k1, g.arrivals);
         __syncthreads();
     }
@@ -424,7 +458,7 @@ int wavefront_units_per_block(const Group &g) {
     return P;
 }
 
-template <int ALGO, int SLOT, int NREG>
+template <int ALGO, int SLOT, int NREG, bool JREG = false>
 static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
                              unsigned *arrivals, cudaStream_t st) {
     const int nch = g.Ltau / C;
@@ -433,28 +467,33 @@ static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, 
     const int blocks = (units + P - 1) / P;
     const size_t sm = (size_t)P * (kRing * SLOT + 2 * g.L * g.L) * sizeof(uint64_t);
     const int threads = P * (g.L * g.L / 2);
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_wavefront<ALGO, SLOT, NREG>,
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_wavefront<ALGO, SLOT, NREG, JREG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_sweep_wavefront<ALGO, SLOT, NREG>, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(k_sweep_wavefront<ALGO, SLOT, NREG, JREG>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  100);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_sweep_wavefront<ALGO, SLOT, NREG><<<blocks, threads, sm, st>>>(g, C, nch, P, sweep_base, sweep, (uint32_t)seed,
+    k_sweep_wavefront<ALGO, SLOT, NREG, JREG><<<blocks, threads, sm, st>>>(g, C, nch, P, sweep_base, sweep, (uint32_t)seed,
                                                                      (uint32_t)(seed >> 32), arrivals);
     return cudaGetLastError();
 }
 
-// Registers are allocated per SM sub-partition (16K each).  Variant 0 caps a
-// thread at 96 registers (two blocks of <= 288 threads per SM), variant 1 at
-// 72 (three blocks); blocks of more than 288 threads get 64.
+// Registers are allocated per SM sub-partition (16K each), so a block of 9
+// warps (288 threads) fits twice per SM at <= 96 registers and three times at
+// <= 72.  Variant 0 (default): 96 registers with the couplings of the
+// thread's sites held in registers for the whole chunk; variant 1: 72
+// registers (three blocks per SM, with spills); variant 2: 96 registers,
+// couplings re-read from shared memory every step.  Blocks of more than 288
+// threads get 64.
 template <int ALGO, int SLOT>
 static cudaError_t launch_wf_slot(const Group &g, int C, const uint32_t *sb, uint32_t sweep, uint64_t seed,
                                   unsigned *arrivals, cudaStream_t st) {
     const int threads = wavefront_units_per_block(g) * (g.L * g.L / 2);
     if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, sb, sweep, seed, arrivals, st);
     if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, sb, sweep, seed, arrivals, st);
-    return launch_wf<ALGO, SLOT, 96>(g, C, sb, sweep, seed, arrivals, st);
+    if (g_wavefront_variant == 2) return launch_wf<ALGO, SLOT, 96>(g, C, sb, sweep, seed, arrivals, st);
+    return launch_wf<ALGO, SLOT, 96, true>(g, C, sb, sweep, seed, arrivals, st);
 }
 
 // Ring planes are padded to the next of a few sizes (exact for L = 8, 12, 16,

@@ -58,7 +58,7 @@ def candidates(shapes, sweeps_per_call):
     chunks = candidate_chunks(shapes)
     persistent = [1, 2] if len(shapes) > 1 else [1]
     graph = [0, sweeps_per_call] if sweeps_per_call > 1 else [0]
-    for chunk, variant, pers, gr in itertools.product(chunks, [0, 1], persistent, graph):
+    for chunk, variant, pers, gr in itertools.product(chunks, [0, 1, 2], persistent, graph):
         yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr}
 
 

@@ -248,7 +248,7 @@ def test_reference_and_wavefront_kernels_agree_at_mid_scale():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("L,R,algo", [(8, 2, Q.HEATBATH), (24, 2, Q.METROPOLIS), (24, 3, Q.HEATBATH),
                                       (32, 2, Q.HEATBATH), (6, 4, Q.METROPOLIS)])
 def test_wavefront_register_variants_match_oracle(variant, L, R, algo):
