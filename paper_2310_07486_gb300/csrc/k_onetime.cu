@@ -71,17 +71,26 @@ __device__ __forceinline__ void overlap_sums(const uint64_t *__restrict__ A, con
 }
 
 template <int L>
-__global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t *__restrict__ P, int triples) {
+__global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint64_t *__restrict__ P, int triples) {
     constexpr int NW = (L * L + 63) / 64, H = L / 2;
     extern __shared__ __align__(16) unsigned char ot_smem[];
     const int R = g.R, Lt = g.Ltau, bd = blockDim.x, tid = threadIdx.x;
     const int npair = R * (R - 1) / 2;
     const bool do3 = triples && R >= 3 && R <= kMaxTripleR;
-    // [pair] per-pair sums of Q^2, then (triples only) [pair][dir][c][thread] and [pair][thread]
+    // [pair] per-pair sums of Q^2; [2][L/2+1][thread] the thread's G and F3 sums
+    // (kept in shared memory to spare registers); then (triples only)
+    // [pair][dir][c][thread] column/row sums and [pair][thread] overlaps
     unsigned long long *ppsh = reinterpret_cast<unsigned long long *>(ot_smem);
-    int8_t *nsh = reinterpret_cast<int8_t *>(ot_smem + (size_t)npair * 8);
-    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + (size_t)npair * 8 + (size_t)npair * 2 * L * bd);
+    long long *accsh = reinterpret_cast<long long *>(ot_smem + (size_t)npair * 8);
+    const size_t o_n = (size_t)npair * 8 + (size_t)2 * (H + 1) * bd * 8;
+    int8_t *nsh = reinterpret_cast<int8_t *>(ot_smem + o_n);
+    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + o_n + (size_t)npair * 2 * L * bd);
     for (int i = tid; i < npair; i += bd) ppsh[i] = 0ull;
+#pragma unroll
+    for (int d = 0; d <= H; ++d) {
+        accsh[(size_t)d * bd + tid] = 0;
+        accsh[(size_t)(H + 1 + d) * bd + tid] = 0;
+    }
     __syncthreads();
     const int pb = blockIdx.x / 64, b = blockIdx.x % 64;
     const int p = p0 + pb, w = p / g.K, j = p % g.K;
@@ -90,13 +99,6 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
 
     long long p2 = 0, t3 = 0;
     unsigned long long p4lo = 0, p4hi = 0;
-    long long gacc[H + 1];
-    long long facc[H + 1];
-#pragma unroll
-    for (int d = 0; d <= H; ++d) {
-        gacc[d] = 0;
-        facc[d] = 0;
-    }
     for (int t = tid; t < Lt; t += bd) {
         int pi = 0;
         for (int ra = 0; ra < R; ++ra)
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
                     int s = 0;
 #pragma unroll
                     for (int c = 0; c < L; ++c) s += nx[c] * nx[(c + d) % L] + ny[c] * ny[(c + d) % L];
-                    gacc[d] += (d == 0 || d == H) ? s : 2 * s;  // G[d] = G[L - d]
+                    accsh[(size_t)d * bd + tid] += (d == 0 || d == H) ? s : 2 * s;  // G[d] = G[L - d]
                 }
                 if (do3) {
 #pragma unroll
@@ -139,6 +141,9 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
                     const long long qab = qsh[(size_t)ab * bd + tid], qbc = qsh[(size_t)bc * bd + tid],
                                     qac = qsh[(size_t)ac * bd + tid];
                     t3 += qab * qbc * qac;
+                    int ft[H + 1];  // this triple's F3 sums (int32: < 6 * 2^10 * 2^16)
+#pragma unroll
+                    for (int d = 0; d <= H; ++d) ft[d] = 0;
                     // the replica shared by the two momentum-carrying overlaps: a, b, c
 #pragma unroll 1
                     for (int rot = 0; rot < 3; ++rot) {
@@ -162,10 +167,12 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
                                                                      : n2[(c + d) % L] + n2[(c + L - d) % L];
                                     s += n1[c] * m;
                                 }
-                                facc[d] += qz * (long long)s;
+                                ft[d] += (int)qz * s;
                             }
                         }
                     }
+#pragma unroll
+                    for (int d = 0; d <= H; ++d) accsh[(size_t)(H + 1 + d) * bd + tid] += ft[d];
                 }
     }
 
@@ -193,8 +200,8 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
     }
 #pragma unroll
     for (int d = 0; d <= H; ++d) {
-        const long long gs = wsum(gacc[d]);
-        const long long fs = wsum(facc[d]);
+        const long long gs = wsum(accsh[(size_t)d * bd + tid]);
+        const long long fs = wsum(accsh[(size_t)(H + 1 + d) * bd + tid]);
         if (lead) {
             atomicAdd(reinterpret_cast<unsigned long long *>(&g.Gacc[idx * (H + 1) + d]), (unsigned long long)gs);
             if (do3)
@@ -206,7 +213,7 @@ __global__ void __launch_bounds__(128) k_onetime(Group g, int p0, const uint64_t
 
 size_t onetime_smem_bytes(const Group &g, int triples, int threads) {
     const int npair = g.R * (g.R - 1) / 2;
-    const size_t pp = (size_t)npair * 8;
+    const size_t pp = (size_t)npair * 8 + (size_t)2 * (g.L / 2 + 1) * threads * 8;
     if (!triples || g.R < 3 || g.R > kMaxTripleR) return pp;
     return pp + (size_t)npair * (2 * g.L + 2) * threads;
 }
