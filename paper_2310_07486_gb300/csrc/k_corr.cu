@@ -91,6 +91,7 @@ __global__ void __launch_bounds__(256) k_gram(Group g, int p0, const uint64_t *P
 // Equal-time overlap of every replica pair at one ladder position.
 cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int triples,
                            int *status, cudaStream_t st) {
+    if (tensor && !gram_tc_fits(g)) tensor = 0;  // very long L_tau: integer pipes
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
     // the tensor-core Gram launch puts (pair, replica, sample bit) on gridDim.y (<= 65535)

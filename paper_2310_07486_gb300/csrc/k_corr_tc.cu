@@ -15,7 +15,8 @@
 //
 // Operands: the x-packed bit planes of the transposed scratch buffer are
 // expanded to E4M3 +-1 (0 for padding) in shared memory, K-major with the
-// 128-byte swizzle, in chunks of 128 sites, double buffered against the MMA.
+// 128-byte swizzle, in chunks of 128 sites, double buffered against the MMA;
+// four spin bits become four bytes with one multiply and one mask.
 #include "qsg_launch.h"
 
 namespace qsg {
@@ -60,11 +61,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 }  // namespace
 
-// 4 bits -> 4 bytes: byte k = 0x80 if bit k is set (isolate bit k in byte k,
-// then carry it to the top of the byte).
-__device__ __forceinline__ uint32_t spread4(uint32_t x) {
-    const uint32_t y = ((x & 0xFu) * 0x01010101u) & 0x08040201u;
-    return (y + 0x7F7F7F7Fu) & 0x80808080u;
+// 4 spin bits -> 4 E4M3 bytes: +1 = 0x38, -1 = 0xB8 (a set bit is spin -1).
+// The multiplier places bit k at bit 8k + 7; the four shifted copies of the
+// nibble do not overlap, so no carry disturbs the kept bits.
+__device__ __forceinline__ uint32_t nibble_e4m3(uint32_t x4) {
+    return ((x4 * 0x10204080u) & 0x80808080u) | 0x38383838u;
 }
 
 __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
@@ -145,21 +146,21 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
 #pragma unroll
             for (int c16 = 0; c16 < 8; ++c16) {
                 const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
-                const uint4 v = make_uint4(spread4(b16) | 0x38383838u, spread4(b16 >> 4) | 0x38383838u,
-                                           spread4(b16 >> 8) | 0x38383838u, spread4(b16 >> 12) | 0x38383838u);
+                const uint4 v = make_uint4(nibble_e4m3(b16 & 0xFu), nibble_e4m3((b16 >> 4) & 0xFu),
+                                           nibble_e4m3((b16 >> 8) & 0xFu), nibble_e4m3((b16 >> 12) & 0xFu));
                 *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = v;
             }
         } else {
 #pragma unroll
             for (int c16 = 0; c16 < 8; ++c16) {
                 const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
-                const int nv = min(max(valid - c16 * 16, 0), 16);
-                const uint32_t v16 = nv >= 16 ? 0xFFFFu : ((1u << nv) - 1u);
                 uint32_t out[4];
 #pragma unroll
                 for (int qq = 0; qq < 4; ++qq) {
-                    const uint32_t keep = (spread4(v16 >> (4 * qq)) >> 7) * 0xFFu;
-                    out[qq] = (spread4(b16 >> (4 * qq)) | 0x38383838u) & keep;
+                    out[qq] = nibble_e4m3((b16 >> (4 * qq)) & 0xFu);
+#pragma unroll
+                    for (int by = 0; by < 4; ++by)
+                        if (c16 * 16 + qq * 4 + by >= valid) out[qq] &= ~(0xFFu << (8 * by));
                 }
                 *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = make_uint4(out[0], out[1], out[2], out[3]);
             }
@@ -302,6 +303,8 @@ size_t gram_tc_smem_bytes(const Group &g) {
     return 1024 + 4 * (size_t)kChunkBytes + 2 * sizeof(int) * (size_t)g.nlag + 16 +
            3 * (size_t)kTile * g.nwx * sizeof(uint64_t);
 }
+
+bool gram_tc_fits(const Group &g) { return gram_tc_smem_bytes(g) <= 227 * 1024; }
 
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st) {
     const int nb = (g.Ltau + kTile - 1) / kTile;

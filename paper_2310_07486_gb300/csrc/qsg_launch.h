@@ -63,6 +63,7 @@ cudaError_t launch_onetime(const Group &g, int p0, int np, const uint64_t *P, in
 // FP64 finish of the one-time observables into g.outO and g.outK.
 cudaError_t launch_onetime_finish(const Group &g, long long n_meas, int triples, cudaStream_t st);
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st);
+bool gram_tc_fits(const Group &g);  // the tensor-core path's shared memory fits one CTA
 
 // FP64 finish into g.outC / g.outQ / g.outP.
 cudaError_t launch_finish(const Group &g, long long n_meas, cudaStream_t st);
