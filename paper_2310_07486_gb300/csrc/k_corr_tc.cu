@@ -26,7 +26,7 @@ namespace {
 constexpr int kTile = 128;          // rows of A (t1) and of B (t2) per tile
 constexpr int kChunk = 128;         // sites (bytes) per K chunk = one swizzled row
 constexpr int kChunkBytes = kTile * kChunk;  // 16 KB per operand chunk
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;  // two threads per tile row (expansion), two warps per TMEM lane quadrant
 constexpr unsigned kSpinLimit = 1u << 22;    // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -99,14 +99,16 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
     const int nchunks = (L2 + kChunk - 1) / kChunk;
     const uint64_t *src = P + ((size_t)sb * 64 + bit) * Lt * nwx;
 
-    // bit rows of block blk into dst (one row per thread; rows past L_tau are zero)
+    // bit rows of block blk into dst (threads < 128, one row each; rows past L_tau are zero)
     auto fetch_rows = [&](uint64_t *dst, int blk) {
-        const int t = blk * kTile + tid;
-        uint64_t *d = dst + tid * nwx;
-        if (t < Lt) {
-            for (int x = 0; x < nwx; ++x) cp_async8(d + x, src + (size_t)t * nwx + x);
-        } else {
-            for (int x = 0; x < nwx; ++x) d[x] = 0ull;
+        if (tid < kTile) {
+            const int t = blk * kTile + tid;
+            uint64_t *d = dst + tid * nwx;
+            if (t < Lt) {
+                for (int x = 0; x < nwx; ++x) cp_async8(d + x, src + (size_t)t * nwx + x);
+            } else {
+                for (int x = 0; x < nwx; ++x) d[x] = 0ull;
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -130,40 +132,32 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
     const uint32_t tmem = tmem_slot;
     const uint32_t idesc = idesc_e4m3_128x128();
 
-    // expand K chunk kc of the bit rows `bits` into a swizzled E4M3 operand chunk
+    // expand K chunk kc of the bit rows `bits` into a swizzled E4M3 operand
+    // chunk; thread = (row, half row of 64 sites = one bit word)
     auto expand = [&](uint8_t *dst, const uint64_t *bits, int blk, int kc) {
-        const int row = tid;
+        const int row = tid >> 1, hh = tid & 1;
         const int t = blk * kTile + row;
-        const int k0 = kc * kChunk;
-        const int w0 = k0 / 64;
-        const uint64_t *b = bits + row * nwx;
-        const uint64_t wlo = w0 < nwx ? b[w0] : 0ull;
-        const uint64_t whi = w0 + 1 < nwx ? b[w0 + 1] : 0ull;
-        const int valid = t < Lt ? min(max(L2 - k0, 0), kChunk) : 0;
+        const int k0 = kc * kChunk + 64 * hh;
+        const int wi = k0 / 64;
+        const uint64_t word = wi < nwx ? bits[row * nwx + wi] : 0ull;
+        const int valid = t < Lt ? min(max(L2 - k0, 0), 64) : 0;
         uint8_t *rowp = dst + row * 128;
         // E4M3: +1 = 0x38, -1 = 0xB8 (set bit = spin -1), 0 for padding sites
-        if (valid == kChunk) {
 #pragma unroll
-            for (int c16 = 0; c16 < 8; ++c16) {
-                const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
-                const uint4 v = make_uint4(nibble_e4m3(b16 & 0xFu), nibble_e4m3((b16 >> 4) & 0xFu),
-                                           nibble_e4m3((b16 >> 8) & 0xFu), nibble_e4m3((b16 >> 12) & 0xFu));
-                *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = v;
-            }
-        } else {
+        for (int gq = 0; gq < 4; ++gq) {
+            const uint32_t b16 = (uint32_t)(word >> (gq * 16));
+            uint32_t out[4];
 #pragma unroll
-            for (int c16 = 0; c16 < 8; ++c16) {
-                const uint32_t b16 = (uint32_t)((c16 < 4 ? wlo : whi) >> ((c16 & 3) * 16));
-                uint32_t out[4];
+            for (int qq = 0; qq < 4; ++qq) out[qq] = nibble_e4m3((b16 >> (4 * qq)) & 0xFu);
+            if (valid < 64) {
 #pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    out[qq] = nibble_e4m3((b16 >> (4 * qq)) & 0xFu);
+                for (int qq = 0; qq < 4; ++qq)
 #pragma unroll
                     for (int by = 0; by < 4; ++by)
-                        if (c16 * 16 + qq * 4 + by >= valid) out[qq] &= ~(0xFFu << (8 * by));
-                }
-                *reinterpret_cast<uint4 *>(rowp + ((c16 ^ (row & 7)) << 4)) = make_uint4(out[0], out[1], out[2], out[3]);
+                        if (gq * 16 + qq * 4 + by >= valid) out[qq] &= ~(0xFFu << (8 * by));
             }
+            *reinterpret_cast<uint4 *>(rowp + (((4 * hh + gq) ^ (row & 7)) << 4)) =
+                make_uint4(out[0], out[1], out[2], out[3]);
         }
     };
 
@@ -171,7 +165,9 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
     int issued[2] = {0, 0};
     int gchunk = 0;
     bool ok = true;
-    const int m = warp * 32 + lane;  // TMEM lane = tile row
+    // epilogue: warp -> TMEM lane quadrant (rows) and one half of the columns
+    const int m = (warp & 3) * 32 + lane;  // TMEM lane = tile row
+    const int cbase = (warp >> 2) * 64;
     const int t1 = i * kTile + m;
 
     for (int jb = i; jb < nb && ok; ++jb) {
@@ -226,9 +222,9 @@ __global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uin
         const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
         const int whigh = g.boundary == 1 ? -1 : 1;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kTile; c0 += 16) {
+        for (int c0 = cbase; c0 < cbase + 64; c0 += 16) {
             uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
