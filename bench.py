@@ -97,6 +97,29 @@ def run_profile_case(name):
     print("ok", name, flush=True)
 
 
+def rank_seed(base_seed, rank):
+    """Seed of a rank's disorder samples: every rank simulates its own samples
+    (weak scaling); no data moves between ranks."""
+    return base_seed + 1000003 * rank
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise maximum of a list of floats over all ranks (the timed
+    region's slowest rank); identity without a process group."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    tt = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.cpu()]
+
+
+def whole_job_rate(units_per_step_per_rank, world, ms_per_step):
+    """Units per ns over all ranks: every rank's units divided by the slowest
+    rank's step time."""
+    return units_per_step_per_rank * world / (ms_per_step * 1e6)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -207,7 +230,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     w = workloads.ALL[args.workload]()
-    seed = w.seed + 1000003 * rank  # each rank simulates its own samples
+    seed = rank_seed(w.seed, rank)
     stream = torch.cuda.current_stream()
     ctx = Q.Context(w.shapes, device=torch.device("cuda", local), stream=stream)
     ctx.qsg_init_samples(seed, w.ladders)
@@ -258,11 +281,8 @@ def run_ours(args, rank, world, local):
     clk = clocks.stop()
     ms = t0.elapsed_time(t1) / args.steps
     sweep_ms = sum(a.elapsed_time(b) for a, b in sweep_events) / (len(sweep_events) * sps)
-    if dist:
-        tt = torch.tensor([ms, sweep_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms, sweep_ms = float(tt[0]), float(tt[1])
-    value = updates_per_step * world / (ms * 1e6)
+    ms, sweep_ms = max_over_ranks([ms, sweep_ms], dist, "cuda")
+    value = whole_job_rate(updates_per_step, world, ms)
 
     # end to end through the C ABI with host buffers: the state is uploaded
     # from pinned host memory, the step runs, the correlators come back
@@ -286,11 +306,8 @@ def run_ours(args, rank, world, local):
                 ctx.qsg_read_correlators(gi)
         torch.cuda.synchronize()
         e2e_ms = (time.perf_counter() - t_start) * 1e3 / args.steps
-        if dist:
-            tt = torch.tensor([e2e_ms], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_ms = float(tt[0])
-        e2e = {"value": updates_per_step * world / (e2e_ms * 1e6), "unit": "spin-flips/ns",
+        e2e_ms = max_over_ranks([e2e_ms], dist, "cuda")[0]
+        e2e = {"value": whole_job_rate(updates_per_step, world, e2e_ms), "unit": "spin-flips/ns",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms}
 
     if rank != 0:
@@ -352,6 +369,7 @@ def oracle_subset(w, n_k, R=None):
     import oracle
     s, lad = w.shapes[0], w.ladders[0]
     R = R or s.n_replicas
+    n_k = min(n_k, len(lad))
     g = oracle.OracleGroup(s.L, s.Ltau, 1, R, n_k, algo=s.algo, boundary=s.boundary)
     g.init(w.seed, lad[:n_k])
     return g, s
