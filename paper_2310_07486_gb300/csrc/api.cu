@@ -20,7 +20,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxA = 16384;               // longest A_i table of the tempering test
-constexpr size_t kScratchCap = 256u << 20;  // bytes of transposed scratch for the correlators
+constexpr size_t kScratchCap = 1024u << 20;  // bytes of correlator scratch (transposed bits, E4M3 rows)
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 

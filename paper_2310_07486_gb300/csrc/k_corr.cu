@@ -14,7 +14,21 @@ size_t measure_scratch_words_per_pair(const Group &g) {
     return (size_t)g.R * 64 * g.Ltau * g.nwx;
 }
 
-// scratch layout for a batch of (w, j) pairs: [pair][r][b][tau][nwx]
+// Bit matrix transpose step of half-size j across lanes l and l ^ j: bits
+// whose index has bit j clear (mask m) stay in the lower row; the lower row
+// takes the partner's low-half bits shifted up, the upper row the partner's
+// high-half bits shifted down.  Five such steps (j = 16 .. 1) and the
+// in-register step j = 32 swap the bits of (row, column): (s, b) -> (b, s).
+template <int J>
+__device__ __forceinline__ uint64_t transpose_step(uint64_t w, bool upper, uint64_t m) {
+    const uint64_t p = __shfl_xor_sync(0xffffffffu, w, J);
+    return upper ? ((w & ~m) | ((p >> J) & m)) : ((w & m) | ((p << J) & ~m));
+}
+
+// scratch layout for a batch of (w, j) pairs: [pair][r][b][tau][nwx].
+// One warp per (slot, tau, 64-site group): lane l loads the multispin words of
+// sites l and l + 32 (bit b = sample b), transposes the 64 x 64 bit block in
+// registers and ends up holding the x-packed words of samples l and l + 32.
 __global__ void k_transpose(Group g, int p0, int npairs, uint64_t *P) {
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -31,19 +45,22 @@ __global__ void k_transpose(Group g, int p0, int npairs, uint64_t *P) {
     const int s0 = gx * 64 + lane, s1 = s0 + 32;
     const uint64_t w0 = s0 < L2 ? src[s0] : 0ull;
     const uint64_t w1 = s1 < L2 ? src[s1] : 0ull;
-    uint64_t keep0 = 0, keep1 = 0;
-#pragma unroll 8
-    for (int b = 0; b < 64; ++b) {
-        const uint32_t lo = __ballot_sync(0xffffffffu, (w0 >> b) & 1ull);
-        const uint32_t hi = __ballot_sync(0xffffffffu, (w1 >> b) & 1ull);
-        const uint64_t word = (uint64_t)lo | ((uint64_t)hi << 32);
-        if (lane == (b & 31)) {
-            if (b < 32) keep0 = word; else keep1 = word;
-        }
-    }
-    uint64_t *dst = P + (size_t)sb * 64 * g.Ltau * g.nwx;
-    dst[((size_t)lane * g.Ltau + t) * g.nwx + gx] = keep0;
-    dst[((size_t)(lane + 32) * g.Ltau + t) * g.nwx + gx] = keep1;
+    // j = 32: rows l and l + 32 are both in this lane
+    uint64_t a0 = (w0 & 0xFFFFFFFFull) | (w1 << 32);
+    uint64_t a1 = (w0 >> 32) | (w1 & 0xFFFFFFFF00000000ull);
+    a0 = transpose_step<16>(a0, lane & 16, 0x0000FFFF0000FFFFull);
+    a1 = transpose_step<16>(a1, lane & 16, 0x0000FFFF0000FFFFull);
+    a0 = transpose_step<8>(a0, lane & 8, 0x00FF00FF00FF00FFull);
+    a1 = transpose_step<8>(a1, lane & 8, 0x00FF00FF00FF00FFull);
+    a0 = transpose_step<4>(a0, lane & 4, 0x0F0F0F0F0F0F0F0Full);
+    a1 = transpose_step<4>(a1, lane & 4, 0x0F0F0F0F0F0F0F0Full);
+    a0 = transpose_step<2>(a0, lane & 2, 0x3333333333333333ull);
+    a1 = transpose_step<2>(a1, lane & 2, 0x3333333333333333ull);
+    a0 = transpose_step<1>(a0, lane & 1, 0x5555555555555555ull);
+    a1 = transpose_step<1>(a1, lane & 1, 0x5555555555555555ull);
+    const size_t row0 = ((size_t)sb * 64 + lane) * g.Ltau + t, row1 = row0 + (size_t)32 * g.Ltau;
+    P[row0 * g.nwx + gx] = a0;
+    P[row1 * g.nwx + gx] = a1;
 }
 
 // One block per (slot of the batch, sample bit): all lags of one sample.
@@ -94,8 +111,6 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
     if (tensor && !gram_tc_fits(g)) tensor = 0;  // very long L_tau: integer pipes
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
-    // the tensor-core Gram launch puts (pair, replica, sample bit) on gridDim.y (<= 65535)
-    if (tensor && batch > 65535 / (g.R * 64)) batch = 65535 / (g.R * 64);
     if (batch < 1) return cudaErrorInvalidValue;
     const int npairs_total = g.W * g.K;
     const size_t sh_bytes = (size_t)g.Ltau * g.nwx * sizeof(uint64_t);

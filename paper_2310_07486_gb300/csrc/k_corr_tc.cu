@@ -7,26 +7,39 @@
 // a dense contraction over the L^2 sites.  The spins are +-1, exact in FP8
 // E4M3, and every partial sum is an integer of magnitude <= L^2 < 2^24, so a
 // tcgen05.mma (kind::f8f6f4, FP32 accumulation in tensor memory) computes G
-// exactly.  Each CTA owns one 128-row block i of one sample and walks the
-// column blocks j >= i (the upper triangle; G is symmetric), folding every
-// element into per-lag bins: pairs with offset o = t2 - t1 feed lag o when
-// o < L_tau/2 and lag L_tau - o (the forward pair from t2, which wraps, so it
-// carries the APBC sign) when o > L_tau/2; o = L_tau/2 counts twice.
+// exactly.  Only the upper triangle of 128 x 128 tiles (i, j >= i) is formed
+// (G is symmetric), and every element is folded into per-lag bins: pairs with
+// offset o = t2 - t1 feed lag o when o < L_tau/2 and lag L_tau - o (the
+// forward pair from t2, which wraps, so it carries the APBC sign) when
+// o > L_tau/2; o = L_tau/2 counts twice.
 //
-// Operands: the x-packed bit planes of the transposed scratch buffer are
-// expanded to E4M3 +-1 (0 for padding) in shared memory, K-major with the
-// 128-byte swizzle, in chunks of 128 sites, double buffered against the MMA;
-// four spin bits become four bytes with one multiply and one mask.
+// One persistent CTA per SM, specialised warps:
+//   producers (8 warps, two threads per tile row) stream the x-packed bit rows
+//     of the transposed scratch through a cp.async ring and expand them to
+//     E4M3 +-1 (0 for padding) in shared memory, K-major with the 128-byte
+//     swizzle, sites in a bit-interleaved order shared by A and B: the A row block once per block (resident while its row of
+//     tiles is multiplied), B in 128-site chunks through a ring of stages;
+//   one thread issues the MMAs into two tensor-memory accumulators, so the
+//     next tile is multiplied while the last one is folded;
+//   the epilogue (8 warps, two per TMEM lane quadrant) folds the tiles into
+//     shared-memory lag bins and flushes them to the int64 sums.
+// The work unit is one sample's row blocks i and nb - 1 - i: nb + 1 tiles for
+// every unit, so a static round robin over the units balances the SMs.
 #include "qsg_launch.h"
 
 namespace qsg {
 
 namespace {
 
-constexpr int kTile = 128;          // rows of A (t1) and of B (t2) per tile
-constexpr int kChunk = 128;         // sites (bytes) per K chunk = one swizzled row
+constexpr int kTile = 128;                   // rows of A (t1) and of B (t2) per tile
+constexpr int kChunk = 128;                  // sites (bytes) per K chunk = one swizzled row
 constexpr int kChunkBytes = kTile * kChunk;  // 16 KB per operand chunk
-constexpr int kThreads = 256;  // two threads per tile row (expansion), two warps per TMEM lane quadrant
+constexpr int kBitsDepth = 8;                // bit-row chunks in flight per producer thread
+constexpr int kMaxStages = 4;                // B stages at most
+constexpr int kProducers = 256;              // warps 0-7: two threads per tile row
+constexpr int kEpilogue = 256;               // warps 8-15: two per TMEM lane quadrant
+constexpr int kMmaWarp = 16;
+constexpr int kThreads = 17 * 32;
 constexpr unsigned kSpinLimit = 1u << 22;    // bounded mbarrier waits
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -47,269 +60,457 @@ __device__ __forceinline__ uint32_t idesc_e4m3_128x128() {
     return (1u << 4) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
-    uint32_t done = 0;
+struct Ctl {
+    uint64_t bfull[kMaxStages], bempty[kMaxStages];  // B stage written / multiplied
+    uint64_t afull, aempty;                          // A block written / multiplied
+    uint64_t accfull[2], accempty[2];                // accumulator computed / folded
+    uint64_t done;                                   // every MMA of the CTA completed
+    uint32_t tmem;
+    int abort;  // a wait gave up: every role skips its work and runs out its loops
+};
+
+// Wait for the phase of the given parity; false (and the abort flag set) when
+// the limit is reached or another thread has given up already.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort) {
+    volatile int *ab = abort;
+    if (*ab) return false;
+    const uint32_t a = smem_u32(bar);
     for (unsigned it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
-                     : "r"(bar), "r"(phase)
+                     : "r"(a), "r"(parity)
                      : "memory");
         if (done) return true;
+        if ((it & 255u) == 255u && *ab) return false;
     }
+    *ab = 1;
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 8-byte copy global -> shared; src_bytes = 0 writes zeros
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
+
+// 32 spin bits -> 32 E4M3 bytes (+1 = 0x38, -1 = 0xB8; a set bit is spin -1)
+// in the site order of the contraction: byte k of output word j is bit
+// 8k + j.  The Gram sums over sites, so any order serves that A and B share;
+// this one takes one shift and one mask per output word.
+__device__ __forceinline__ uint32_t spread_e4m3(uint32_t b, int j) {
+    return ((b << (7 - j)) & 0x80808080u) | 0x38383838u;
+}
+
+// Bytes of spread_e4m3's output word j whose bits are set in the site mask vm
+// are 0xFF, the others 0.
+__device__ __forceinline__ uint32_t spread_mask(uint32_t vm, int j) {
+    return (((vm << (7 - j)) & 0x80808080u) >> 7) * 0xFFu;
+}
+
+// The work of one CTA: units u = blockIdx.x + n gridDim.x; unit u is sample
+// u / nhalf, row blocks h = u % nhalf and nb - 1 - h (one block when equal).
+// Within a unit the blocks are items; item i has the tiles (i, jb), jb >= i.
+// The producer's chunk sequence per item: A chunks kc = 0..nc-1 of block i,
+// then B chunks kc of blocks jb = i+1..nb-1 (tile (i, i) takes B = A).
+struct Cursor {
+    int u, sidx, h, item, i, jb, kc;
+    bool valid;
+};
+
+__device__ __forceinline__ int item_block(int h, int item, int nb) { return item ? nb - 1 - h : h; }
+__device__ __forceinline__ int unit_items(int h, int nb) { return nb - 1 - h != h ? 2 : 1; }
+
+__device__ __forceinline__ void cursor_unit(Cursor &c, int nunits, int nhalf) {
+    c.valid = c.u < nunits;
+    c.sidx = c.u / nhalf;
+    c.h = c.u - c.sidx * nhalf;
+    c.item = 0;
+    c.i = c.h;
+    c.jb = c.h;
+    c.kc = 0;
+}
+
+__device__ __forceinline__ void cursor_start(Cursor &c, int nunits, int nhalf) {
+    c.u = blockIdx.x;
+    cursor_unit(c, nunits, nhalf);
+}
+
+__device__ __forceinline__ void cursor_next(Cursor &c, int nunits, int nhalf, int nb, int nc) {
+    if (++c.kc < nc) return;
+    c.kc = 0;
+    if (++c.jb < nb) return;
+    if (++c.item >= unit_items(c.h, nb)) {
+        c.u += gridDim.x;
+        cursor_unit(c, nunits, nhalf);
+        return;
+    }
+    c.i = item_block(c.h, c.item, nb);
+    c.jb = c.i;
+}
+
+// FP32 accumulator holding an integer |x| < 2^22 -> int32 with one add: in
+// [2^23, 2^24) the FP32 spacing is 1, so x + 1.5 * 2^23 is exact and its bit
+// pattern is that of 1.5 * 2^23 plus x.
+__device__ __forceinline__ int exact_f32_to_int(uint32_t bits) {
+    return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
 }  // namespace
 
-// 4 spin bits -> 4 E4M3 bytes: +1 = 0x38, -1 = 0xB8 (a set bit is spin -1).
-// The multiplier places bit k at bit 8k + 7; the four shifted copies of the
-// nibble do not overlap, so no carry disturbs the kept bits.
-__device__ __forceinline__ uint32_t nibble_e4m3(uint32_t x4) {
-    return ((x4 * 0x10204080u) & 0x80808080u) | 0x38383838u;
-}
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-
-// grid: (row blocks nb, slot-bits of the batch); P: [slot_b][bit][Ltau][nwx].
-// Shared memory: operand chunks [2 buffers][A, B][16 KB] (1024-aligned), the
-// lag bins, and the bit rows of the A block and of two B blocks (the next one
-// is fetched while the current one is multiplied).
-__global__ void __launch_bounds__(kThreads) k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nb,
-                                                      int *status) {
+// P: [sample][Ltau][nwx] transposed bits of the batch (sample = (pair, r, bit)).
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int *status) {
     extern __shared__ __align__(16) uint8_t dyn_raw[];
     uint8_t *dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
-    const int Lt = g.Ltau, nwx = g.nwx, L2 = g.L * g.L, half = Lt / 2;
-    uint8_t *sbuf = dyn;
-    int *binC = reinterpret_cast<int *>(dyn + 4 * kChunkBytes);
-    int *binQ = binC + g.nlag;
-    uint64_t *bitsA = reinterpret_cast<uint64_t *>(binQ + g.nlag);
-    bitsA = reinterpret_cast<uint64_t *>((reinterpret_cast<uintptr_t>(bitsA) + 15) & ~(uintptr_t)15);
-    uint64_t *bitsB = bitsA + kTile * nwx;  // [2][kTile][nwx]
-    __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ uint32_t tmem_slot;
+    __shared__ Ctl ctl;
+    const int Lt = g.Ltau, L2 = g.L * g.L, half = Lt / 2, nl = g.nlag, nwx = g.nwx;
+    const int nb = (Lt + kTile - 1) / kTile, nhalf = (nb + 1) / 2;
+    const int nc = (L2 + kChunk - 1) / kChunk;
+    const int nunits = nsamples * nhalf;
+    uint8_t *sA = dyn;
+    uint8_t *sB = sA + (size_t)nc * kChunkBytes;
+    uint64_t *ring = reinterpret_cast<uint64_t *>(sB + (size_t)nstages * kChunkBytes);  // [depth][128 rows][2 words]
+    int *binC = reinterpret_cast<int *>(ring + kBitsDepth * kTile * 2);
+    unsigned *binQ = reinterpret_cast<unsigned *>(binC + nl);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i = blockIdx.x;
-    const int sbb = blockIdx.y;
-    const int sb = sbb / 64, bit = sbb % 64;
-    const int pb = sb / g.R, r = sb % g.R;
-    const int pidx = p0 + pb, w = pidx / g.K, j = pidx % g.K;
-    const int nchunks = (L2 + kChunk - 1) / kChunk;
-    const uint64_t *src = P + ((size_t)sb * 64 + bit) * Lt * nwx;
-
-    // bit rows of block blk into dst (threads < 128, one row each; rows past L_tau are zero)
-    auto fetch_rows = [&](uint64_t *dst, int blk) {
-        if (tid < kTile) {
-            const int t = blk * kTile + tid;
-            uint64_t *d = dst + tid * nwx;
-            if (t < Lt) {
-                for (int x = 0; x < nwx; ++x) cp_async8(d + x, src + (size_t)t * nwx + x);
-            } else {
-                for (int x = 0; x < nwx; ++x) d[x] = 0ull;
-            }
+    if (tid == 0) {
+        for (int s = 0; s < kMaxStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.bfull[s])), "r"(kProducers));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.bempty[s])));
         }
-        asm volatile("cp.async.commit_group;\n" ::: "memory");
-    };
-
-    fetch_rows(bitsA, i);
-    fetch_rows(bitsB, i);
-    for (int l = tid; l < g.nlag; l += kThreads) binC[l] = binQ[l] = 0;
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(&tmem_slot)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.afull)), "r"(kProducers));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.aempty)));
+        for (int a = 0; a < 2; ++a) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.accfull[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.accempty[a])), "r"(kEpilogue));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.done)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n");
+        ctl.abort = 0;
+    }
+    if (warp == kMmaWarp) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(&ctl.tmem)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar[1])));
-        asm volatile("fence.mbarrier_init.release.cluster;\n");
+    for (int l = tid; l < nl; l += kThreads) {
+        binC[l] = 0;
+        binQ[l] = 0u;
     }
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    const uint32_t tmem = tmem_slot;
-    const uint32_t idesc = idesc_e4m3_128x128();
+    const uint32_t tmem = ctl.tmem;
 
-    // expand K chunk kc of the bit rows `bits` into a swizzled E4M3 operand
-    // chunk; thread = (row, half row of 64 sites = one bit word)
-    auto expand = [&](uint8_t *dst, const uint64_t *bits, int blk, int kc) {
+    if (warp < kProducers / 32) {
+        // ------------------------------------------------------------ producers
+        // thread (row, hh): sites 64 hh .. 64 hh + 63 of each chunk of the row
         const int row = tid >> 1, hh = tid & 1;
-        const int t = blk * kTile + row;
-        const int k0 = kc * kChunk + 64 * hh;
-        const int wi = k0 / 64;
-        const uint64_t word = wi < nwx ? bits[row * nwx + wi] : 0ull;
-        const int valid = t < Lt ? min(max(L2 - k0, 0), 64) : 0;
-        uint8_t *rowp = dst + row * 128;
-        // E4M3: +1 = 0x38, -1 = 0xB8 (set bit = spin -1), 0 for padding sites
-#pragma unroll
-        for (int gq = 0; gq < 4; ++gq) {
-            const uint32_t b16 = (uint32_t)(word >> (gq * 16));
-            uint32_t out[4];
-#pragma unroll
-            for (int qq = 0; qq < 4; ++qq) out[qq] = nibble_e4m3((b16 >> (4 * qq)) & 0xFu);
-            if (valid < 64) {
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq)
-#pragma unroll
-                    for (int by = 0; by < 4; ++by)
-                        if (gq * 16 + qq * 4 + by >= valid) out[qq] &= ~(0xFFu << (8 * by));
+        Cursor fetch, use;
+        cursor_start(fetch, nunits, nhalf);
+        use = fetch;
+        auto issue = [&](int slot) {
+            if (fetch.valid && !*(volatile int *)&ctl.abort) {
+                const int t = fetch.jb * kTile + row;
+                const int wd = 2 * fetch.kc + hh;
+                const uint64_t *src = P + ((size_t)fetch.sidx * Lt + (t < Lt ? t : Lt - 1)) * nwx + (wd < nwx ? wd : 0);
+                cp_async8(ring + ((size_t)slot * kTile + row) * 2 + hh, src, (t < Lt && wd < nwx) ? 8 : 0);
             }
-            *reinterpret_cast<uint4 *>(rowp + (((4 * hh + gq) ^ (row & 7)) << 4)) =
-                make_uint4(out[0], out[1], out[2], out[3]);
-        }
-    };
-
-    uint32_t phase[2] = {0, 0};
-    int issued[2] = {0, 0};
-    int gchunk = 0;
-    bool ok = true;
-    // epilogue: warp -> TMEM lane quadrant (rows) and one half of the columns
-    const int m = (warp & 3) * 32 + lane;  // TMEM lane = tile row
-    const int cbase = (warp >> 2) * 64;
-    const int t1 = i * kTile + m;
-
-    for (int jb = i; jb < nb && ok; ++jb) {
-        const uint64_t *bb = bitsB + (size_t)((jb - i) & 1) * kTile * nwx;
-        // fetch the next B block while this one is multiplied
-        if (jb + 1 < nb) fetch_rows(bitsB + (size_t)((jb + 1 - i) & 1) * kTile * nwx, jb + 1);
-        for (int kc = 0; kc < nchunks; ++kc, ++gchunk) {
-            const int buf = gchunk & 1;
-            bool mine = true;
-            if (issued[buf]) {
-                mine = mbar_wait(smem_u32(&mbar[buf]), phase[buf]);
-                phase[buf] ^= 1u;
-                issued[buf] = 0;
+            asm volatile("cp.async.commit_group;\n" ::: "memory");
+            if (fetch.valid) cursor_next(fetch, nunits, nhalf, nb, nc);
+        };
+        for (int d = 0; d < kBitsDepth; ++d) issue(d);
+        // aempty / bempty[s] parities: the first use of a buffer waits for the
+        // phase before the first (complete at initialisation)
+        uint32_t a_par = 1u, b_par = 1u;
+        int s = 0;
+        for (uint32_t q = 0; use.valid; ++q) {
+            const int slot = (int)(q & (kBitsDepth - 1));
+            asm volatile("cp.async.wait_group %0;\n" ::"n"(kBitsDepth - 1) : "memory");
+            const uint64_t wv = ring[((size_t)slot * kTile + row) * 2 + hh];
+            const bool isA = use.jb == use.i;
+            uint8_t *dst;
+            bool ok = true;
+            if (isA) {
+                if (use.kc == 0) ok = mbar_wait(&ctl.aempty, a_par, &ctl.abort);
+                dst = sA + (size_t)use.kc * kChunkBytes;
+            } else {
+                ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort);
+                dst = sB + (size_t)s * kChunkBytes;
             }
-            ok = __syncthreads_and(mine) != 0;
-            if (!ok) break;
-            uint8_t *sA = sbuf + buf * 2 * kChunkBytes, *sB = sA + kChunkBytes;
-            expand(sA, bitsA, i, kc);
-            expand(sB, bb, jb, kc);
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;\n");
+            if (ok) {
+                const int t = use.jb * kTile + row;
+                // sites of this thread's 64 that lie inside the lattice (0 past L_tau)
+                const int valid = t < Lt ? L2 - use.kc * kChunk - 64 * hh : 0;
+                uint8_t *rowp = dst + row * kChunk;
+                // output words 8 e + j (e = half of the 64-bit word, j = 0..7)
+                // fill granules 4 hh + 2 e + (j >> 2)
 #pragma unroll
-                for (int kk = 0; kk < kChunk / 32; ++kk) {
-                    const uint64_t da = sdesc_sw128(smem_u32(sA) + kk * 32);
-                    const uint64_t db = sdesc_sw128(smem_u32(sB) + kk * 32);
-                    const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-                    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                for (int e = 0; e < 2; ++e) {
+                    const uint32_t b = (uint32_t)(wv >> (32 * e));
+                    uint32_t o[8];
+#pragma unroll
+                    for (int jj = 0; jj < 8; ++jj) o[jj] = spread_e4m3(b, jj);
+                    if (valid < 64) {  // sites 32 e + 8 k + j of this thread's 64
+                        const int v32 = valid - 32 * e;
+                        const uint32_t vm = v32 >= 32 ? 0xFFFFFFFFu : (v32 <= 0 ? 0u : (1u << v32) - 1u);
+#pragma unroll
+                        for (int jj = 0; jj < 8; ++jj) o[jj] &= spread_mask(vm, jj);
+                    }
+#pragma unroll
+                    for (int hq = 0; hq < 2; ++hq) {
+                        const int gr = 4 * hh + 2 * e + hq;
+                        *reinterpret_cast<uint4 *>(rowp + ((gr ^ (row & 7)) << 4)) =
+                            make_uint4(o[4 * hq], o[4 * hq + 1], o[4 * hq + 2], o[4 * hq + 3]);
+                    }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
-                    smem_u32(&mbar[buf])));
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            issued[buf] = 1;
+            if (isA) {
+                if (use.kc == nc - 1) {
+                    mbar_arrive(&ctl.afull);
+                    a_par ^= 1u;
+                }
+            } else {
+                mbar_arrive(&ctl.bfull[s]);
+                if (++s == nstages) {
+                    s = 0;
+                    b_par ^= 1u;
+                }
+            }
+            issue(slot);
+            cursor_next(use, nunits, nhalf, nb, nc);
         }
-        if (!ok) break;
-        const int lastbuf = (gchunk - 1) & 1;
-        const bool mine = mbar_wait(smem_u32(&mbar[lastbuf]), phase[lastbuf]);
-        phase[lastbuf] ^= 1u;
-        issued[lastbuf] = 0;
-        ok = __syncthreads_and(mine) != 0;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        // offsets o = t2 - t1 of this tile lie in [omin, omax]; most tiles map
-        // every element to lag o (all o < L_tau/2) or to lag L_tau - o (all o >
-        // L_tau/2), only the tiles around L_tau/2 need the per-element choice
-        const int obase = (jb - i) * kTile;
-        const int omin = jb == i ? 1 : obase - (kTile - 1), omax = obase + kTile - 1;
-        const bool full = (jb + 1) * kTile <= Lt && (i + 1) * kTile <= Lt;
-        const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else if (warp < kMmaWarp) {
+        // ------------------------------------------------------------- epilogue
+        const int etid = tid - kProducers;
+        const int quad = warp & 3;                       // TMEM lanes 32 quad .. 32 quad + 31
+        const int cbase = ((warp - kProducers / 32) >> 2) * 64;  // column half of the tile
+        const int m = quad * 32 + lane;                  // tile row
         const int whigh = g.boundary == 1 ? -1 : 1;
-#pragma unroll 1
-        for (int c0 = cbase; c0 < cbase + 64; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-            const int o0 = obase + c0 - m;  // offset of column q is o0 + q
-            if (full && cls == 0 && jb != i) {
+        uint32_t n_t = 0;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const int sidx = u / nhalf, h = u % nhalf;
+            for (int item = 0; item < unit_items(h, nb); ++item) {
+                const int i = item_block(h, item, nb);
+                const int t1 = i * kTile + m;
+                for (int jb = i; jb < nb; ++jb, ++n_t) {
+                    const int a = (int)(n_t & 1u);
+                    const bool ok = mbar_wait(&ctl.accfull[a], (n_t >> 1) & 1u, &ctl.abort);
+                    asm volatile("tcgen05.fence::after_thread_sync;\n");
+                    if (ok) {
+                        // offsets o = t2 - t1 of this tile lie in [omin, omax]; most
+                        // tiles map every element to lag o (all o < L_tau/2) or to lag
+                        // L_tau - o (all o > L_tau/2), only the tiles around L_tau/2
+                        // need the per-element choice
+                        const int obase = (jb - i) * kTile;
+                        const int omin = jb == i ? 1 : obase - (kTile - 1), omax = obase + kTile - 1;
+                        const bool full = (jb + 1) * kTile <= Lt && (i + 1) * kTile <= Lt;
+                        const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
+                        uint32_t v[64];
+                        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + cbase);
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int gv = __float2int_rn(__uint_as_float(v[q]));
-                    atomicAdd(&binC[o0 + q], gv);
-                    atomicAdd(&binQ[o0 + q], gv * gv);
-                }
-            } else if (full && cls == 1) {
+                        for (int c = 0; c < 64; c += 16)
+                            asm volatile(
+                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                                : "=r"(v[c + 0]), "=r"(v[c + 1]), "=r"(v[c + 2]), "=r"(v[c + 3]), "=r"(v[c + 4]),
+                                  "=r"(v[c + 5]), "=r"(v[c + 6]), "=r"(v[c + 7]), "=r"(v[c + 8]), "=r"(v[c + 9]),
+                                  "=r"(v[c + 10]), "=r"(v[c + 11]), "=r"(v[c + 12]), "=r"(v[c + 13]), "=r"(v[c + 14]),
+                                  "=r"(v[c + 15])
+                                : "r"(taddr + (uint32_t)c));
+                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+                        // the accumulator is free for the tile after next
+                        asm volatile("tcgen05.fence::before_thread_sync;\n");
+                        mbar_arrive(&ctl.accempty[a]);
+                        const int o0 = obase + cbase - m;  // offset of column q is o0 + q
+                        if (full && cls == 0 && jb != i) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int gv = __float2int_rn(__uint_as_float(v[q]));
-                    atomicAdd(&binC[Lt - o0 - q], whigh * gv);
-                    atomicAdd(&binQ[Lt - o0 - q], gv * gv);
-                }
-            } else if (t1 < Lt) {
+                            for (int q = 0; q < 64; ++q) {
+                                const int gv = exact_f32_to_int(v[q]);
+                                atomicAdd(&binC[o0 + q], gv);
+                                atomicAdd(&binQ[o0 + q], (unsigned)(gv * gv));
+                            }
+                        } else if (full && cls == 1) {
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int t2 = jb * kTile + c0 + q;
-                    const int o = o0 + q;
-                    if (t2 < Lt && o > 0) {
-                        const int gv = __float2int_rn(__uint_as_float(v[q]));
-                        int lag, wc, wq;
-                        if (o < half) {
-                            lag = o; wc = 1; wq = 1;
-                        } else if (o == half) {
-                            lag = half; wc = g.boundary == 1 ? 0 : 2; wq = 2;
-                        } else {
-                            lag = Lt - o; wc = whigh; wq = 1;
+                            for (int q = 0; q < 64; ++q) {
+                                const int gv = exact_f32_to_int(v[q]);
+                                atomicAdd(&binC[Lt - o0 - q], whigh * gv);
+                                atomicAdd(&binQ[Lt - o0 - q], (unsigned)(gv * gv));
+                            }
+                        } else if (t1 < Lt) {
+#pragma unroll
+                            for (int q = 0; q < 64; ++q) {
+                                const int t2 = jb * kTile + cbase + q;
+                                const int o = o0 + q;
+                                if (t2 < Lt && o > 0) {
+                                    const int gv = exact_f32_to_int(v[q]);
+                                    int lag, wc, wq;
+                                    if (o < half) {
+                                        lag = o; wc = 1; wq = 1;
+                                    } else if (o == half) {
+                                        lag = half; wc = g.boundary == 1 ? 0 : 2; wq = 2;
+                                    } else {
+                                        lag = Lt - o; wc = whigh; wq = 1;
+                                    }
+                                    atomicAdd(&binC[lag], wc * gv);
+                                    atomicAdd(&binQ[lag], (unsigned)(wq * gv * gv));
+                                }
+                            }
                         }
-                        atomicAdd(&binC[lag], wc * gv);
-                        atomicAdd(&binQ[lag], wq * gv * gv);
+                    } else {
+                        asm volatile("tcgen05.fence::before_thread_sync;\n");
+                        mbar_arrive(&ctl.accempty[a]);
                     }
                 }
             }
+            // the unit's bins are complete: add them to the sample's int64 sums;
+            // a CTA's t1 span two row blocks, so a bin holds at most 2 x 256
+            // products G^2 <= 2^20 (L <= 32): 2^29, exact in 32 bits
+            asm volatile("bar.sync 1, %0;\n" ::"n"(kEpilogue) : "memory");
+            const int sb = sidx / 64, bit = sidx % 64;
+            const int pb = sb / g.R, r = sb % g.R;
+            const int pidx = p0 + pb, w = pidx / g.K, j = pidx % g.K;
+            const size_t gbase = ((((size_t)r * g.W * 64) + (size_t)w * 64 + bit) * g.K + j) * nl;
+            const bool write = !*(volatile int *)&ctl.abort;
+            for (int l = etid; l < nl; l += kEpilogue) {
+                long long c = binC[l];
+                unsigned long long qv = binQ[l];
+                // the diagonal (lag 0) is G(t, t) = L^2 for every t: once per sample
+                if (l == 0 && h == 0) {
+                    c += (long long)Lt * L2;
+                    qv += (unsigned long long)Lt * L2 * L2;
+                }
+                if (write && c) atomicAdd(reinterpret_cast<unsigned long long *>(&g.Cacc[gbase + l]), (unsigned long long)c);
+                if (write && qv) atomicAdd(reinterpret_cast<unsigned long long *>(&g.Qacc[gbase + l]), qv);
+                binC[l] = 0;
+                binQ[l] = 0u;
+            }
+            asm volatile("bar.sync 1, %0;\n" ::"n"(kEpilogue) : "memory");
         }
-        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n");
-        __syncthreads();  // next B rows visible; the next tile may overwrite the accumulator
+    } else {
+        // ------------------------------------------------------------------ MMA
+        const uint32_t idesc = idesc_e4m3_128x128();
+        uint32_t a_par = 0u, b_par = 0u, n_t = 0;
+        int bs = 0;
+        bool issued = false;
+        for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const int h = u % nhalf;
+            for (int item = 0; item < unit_items(h, nb); ++item) {
+                const int i = item_block(h, item, nb);
+                const bool a_ok = mbar_wait(&ctl.afull, a_par, &ctl.abort);
+                asm volatile("tcgen05.fence::after_thread_sync;\n");
+                for (int jb = i; jb < nb; ++jb, ++n_t) {
+                    const int a = (int)(n_t & 1u);
+                    bool ok = a_ok && mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort);
+                    asm volatile("tcgen05.fence::after_thread_sync;\n");
+                    for (int kc = 0; kc < nc; ++kc) {
+                        const uint32_t abase = smem_u32(sA + (size_t)kc * kChunkBytes);
+                        uint32_t bbase = abase;
+                        if (jb != i) {
+                            ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort) && ok;
+                            asm volatile("tcgen05.fence::after_thread_sync;\n");
+                            bbase = smem_u32(sB + (size_t)bs * kChunkBytes);
+                        }
+                        if (ok && lane == 0) {
+#pragma unroll
+                            for (int kk = 0; kk < kChunk / 32; ++kk) {
+                                const uint64_t da = sdesc_sw128(abase + kk * 32);
+                                const uint64_t db = sdesc_sw128(bbase + kk * 32);
+                                const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
+                                asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                                 tmem + (uint32_t)(a * kTile)),
+                                             "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                            }
+                            issued = true;
+                        }
+                        if (jb != i) {
+                            if (lane == 0) mma_commit(&ctl.bempty[bs]);
+                            if (++bs == nstages) {
+                                bs = 0;
+                                b_par ^= 1u;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                    if (lane == 0) mma_commit(&ctl.accfull[a]);
+                    __syncwarp();
+                }
+                if (lane == 0) mma_commit(&ctl.aempty);
+                __syncwarp();
+                a_par ^= 1u;
+            }
+        }
+        // every MMA issued has completed before the tensor memory is released
+        // (a commit tracks all earlier MMAs of the issuing thread)
+        if (lane == 0) {
+            mma_commit(&ctl.done);
+            if (issued) {
+                uint32_t done = 0;
+                for (unsigned it = 0; it < kSpinLimit && !done; ++it)
+                    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\nselp.u32 %0, 1, 0, p;\n}\n"
+                                 : "=r"(done)
+                                 : "r"(smem_u32(&ctl.done))
+                                 : "memory");
+                if (!done) ctl.abort = 1;
+            }
+        }
+        __syncwarp();
     }
-    const bool failed = !ok;
-    for (int b = 0; b < 2; ++b)
-        if (issued[b]) mbar_wait(smem_u32(&mbar[b]), phase[b]);
-    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
-    if (failed) {
-        if (tid == 0) atomicExch(status, DEVERR_TIMEOUT);
-        return;
-    }
-    // the diagonal (lag 0) is G(t, t) = L^2 for every t: added once per sample
-    const size_t base = ((((size_t)r * g.W * 64) + (size_t)w * 64 + bit) * g.K + j) * g.nlag;
-    for (int l = tid; l < g.nlag; l += kThreads) {
-        long long c = binC[l], q = binQ[l];
-        if (l == 0 && i == 0) {
-            c += (long long)Lt * L2;
-            q += (long long)Lt * L2 * L2;
-        }
-        if (c) atomicAdd(reinterpret_cast<unsigned long long *>(&g.Cacc[base + l]), (unsigned long long)c);
-        if (q) atomicAdd(reinterpret_cast<unsigned long long *>(&g.Qacc[base + l]), (unsigned long long)q);
-    }
+    asm volatile("tcgen05.fence::after_thread_sync;\n");
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+    if (tid == 0 && ctl.abort) atomicExch(status, DEVERR_TIMEOUT);
 }
 
-size_t gram_tc_smem_bytes(const Group &g) {
-    return 1024 + 4 * (size_t)kChunkBytes + 2 * sizeof(int) * (size_t)g.nlag + 16 +
-           3 * (size_t)kTile * g.nwx * sizeof(uint64_t);
+namespace {
+
+size_t gram_tc_smem_bytes(const Group &g, int nstages) {
+    const int nc = (g.L * g.L + kChunk - 1) / kChunk;
+    return 1024 + (size_t)(nc + nstages) * kChunkBytes + (size_t)kBitsDepth * kTile * 2 * sizeof(uint64_t) +
+           2 * sizeof(int) * (size_t)g.nlag;
 }
 
-bool gram_tc_fits(const Group &g) { return gram_tc_smem_bytes(g) <= 227 * 1024; }
+constexpr size_t kSmemLimit = 227 * 1024;
+
+int gram_tc_stages(const Group &g) {
+    for (int s = kMaxStages; s >= 2; --s)
+        if (gram_tc_smem_bytes(g, s) <= kSmemLimit) return s;
+    return 0;
+}
+
+}  // namespace
+
+bool gram_tc_fits(const Group &g) { return gram_tc_stages(g) >= 2; }
 
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st) {
-    const int nb = (g.Ltau + kTile - 1) / kTile;
-    const size_t sm = gram_tc_smem_bytes(g);
+    const int nstages = gram_tc_stages(g);
+    if (nstages < 2) return cudaErrorInvalidValue;
+    const size_t sm = gram_tc_smem_bytes(g, nstages);
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    dim3 grid(nb, npairs * g.R * 64);
+    int dev = 0, nsm = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int nsamples = npairs * g.R * 64;
+    const int nb = (g.Ltau + kTile - 1) / kTile;
+    const long long nunits = (long long)nsamples * ((nb + 1) / 2);
+    const int grid = (int)(nunits < nsm ? nunits : nsm);
     count_launches(1);
-    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nb, status);
+    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, nstages, status);
     return cudaGetLastError();
 }
 

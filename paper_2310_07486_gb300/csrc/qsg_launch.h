@@ -62,6 +62,8 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
 cudaError_t launch_onetime(const Group &g, int p0, int np, const uint64_t *P, int triples, cudaStream_t st);
 // FP64 finish of the one-time observables into g.outO and g.outK.
 cudaError_t launch_onetime_finish(const Group &g, long long n_meas, int triples, cudaStream_t st);
+// Tensor-core Gram path over the transposed bits P of a batch: folds every
+// 128 x 128 tile of the Gram matrices into the lag sums.
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st);
 bool gram_tc_fits(const Group &g);  // the tensor-core path's shared memory fits one CTA
 
