@@ -14,11 +14,13 @@
 // o > L_tau/2; o = L_tau/2 counts twice.
 //
 // One persistent CTA per SM, specialised warps:
-//   producers (8 warps, two threads per tile row) stream the x-packed bit rows
-//     of the transposed scratch through a cp.async ring and expand them to
-//     E4M3 +-1 (0 for padding) in shared memory, K-major with the 128-byte
-//     swizzle, sites in a bit-interleaved order shared by A and B: the A row block once per block (resident while its row of
-//     tiles is multiplied), B in 128-site chunks through a ring of stages;
+//   producers (8 warps, two threads per tile row) load the x-packed bit rows
+//     of the transposed scratch one row block ahead into registers and expand
+//     them to E4M3 +-1 (0 for padding) in shared memory, K-major with the
+//     128-byte swizzle, sites in a bit-interleaved order shared by A and B:
+//     the A row block once (resident, double buffered where shared memory
+//     allows, while its row of tiles is multiplied), B in 128-site chunks
+//     through a ring of stages;
 //   one thread issues the MMAs into two tensor-memory accumulators, so the
 //     next tile is multiplied while the last one is folded;
 //   the epilogue (8 warps, two per TMEM lane quadrant) folds the tiles into
@@ -34,9 +36,11 @@ namespace {
 constexpr int kTile = 128;                   // rows of A (t1) and of B (t2) per tile
 constexpr int kChunk = 128;                  // sites (bytes) per K chunk = one swizzled row
 constexpr int kChunkBytes = kTile * kChunk;  // 16 KB per operand chunk
-constexpr int kBitsDepth = 8;                // bit-row chunks in flight per producer thread
-constexpr int kMaxStages = 4;                // B stages at most
+constexpr int kMaxNc = 8;                    // 128-site chunks of a row at most (L <= 32)
+constexpr int kMaxStages = 6;                // B stages at most
 constexpr int kProducers = 256;              // warps 0-7: two threads per tile row
+constexpr int kProducerWarps = kProducers / 32;
+constexpr int kEpilogueWarps = 8;
 constexpr int kEpilogue = 256;               // warps 8-15: two per TMEM lane quadrant
 constexpr int kMmaWarp = 16;
 constexpr int kThreads = 17 * 32;
@@ -62,7 +66,7 @@ __device__ __forceinline__ uint32_t idesc_e4m3_128x128() {
 
 struct Ctl {
     uint64_t bfull[kMaxStages], bempty[kMaxStages];  // B stage written / multiplied
-    uint64_t afull, aempty;                          // A block written / multiplied
+    uint64_t afull[2], aempty[2];                    // A buffer written / multiplied
     uint64_t accfull[2], accempty[2];                // accumulator computed / folded
     uint64_t done;                                   // every MMA of the CTA completed
     uint32_t tmem;
@@ -97,12 +101,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 8-byte copy global -> shared; src_bytes = 0 writes zeros
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(smem_u32(smem)), "l"(gmem), "r"(src_bytes)
-                 : "memory");
-}
-
 // 32 spin bits -> 32 E4M3 bytes (+1 = 0x38, -1 = 0xB8; a set bit is spin -1)
 // in the site order of the contraction: byte k of output word j is bit
 // 8k + j.  The Gram sums over sites, so any order serves that A and B share;
@@ -117,45 +115,96 @@ __device__ __forceinline__ uint32_t spread_mask(uint32_t vm, int j) {
     return (((vm << (7 - j)) & 0x80808080u) >> 7) * 0xFFu;
 }
 
+// The 64 sites of word wv into granules 4 hh .. 4 hh + 3 of the swizzled
+// 128-byte row `row` at rowp; sites >= valid (outside the lattice, or every
+// site of a row past L_tau) become 0.  Output words 8 e + j (e = half of the
+// word) fill granules 4 hh + 2 e + (j >> 2).
+__device__ __forceinline__ void expand_full(uint8_t *rowp, uint64_t wv, int hh, int row) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const uint32_t b = (uint32_t)(wv >> (32 * e));
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+            const int gr = 4 * hh + 2 * e + hq;
+            *reinterpret_cast<uint4 *>(rowp + ((gr ^ (row & 7)) << 4)) =
+                make_uint4(spread_e4m3(b, 4 * hq), spread_e4m3(b, 4 * hq + 1), spread_e4m3(b, 4 * hq + 2),
+                           spread_e4m3(b, 4 * hq + 3));
+        }
+    }
+}
+
+__device__ __noinline__ void expand_part(uint8_t *rowp, uint64_t wv, int valid, int hh, int row) {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const uint32_t b = (uint32_t)(wv >> (32 * e));
+        const int v32 = valid - 32 * e;
+        const uint32_t vm = v32 >= 32 ? 0xFFFFFFFFu : (v32 <= 0 ? 0u : (1u << v32) - 1u);
+#pragma unroll
+        for (int hq = 0; hq < 2; ++hq) {
+            const int gr = 4 * hh + 2 * e + hq;
+            uint32_t o[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = spread_e4m3(b, 4 * hq + k) & spread_mask(vm, 4 * hq + k);
+            *reinterpret_cast<uint4 *>(rowp + ((gr ^ (row & 7)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
+        }
+    }
+}
+
+__device__ __forceinline__ void expand_word(uint8_t *rowp, uint64_t wv, int valid, int hh, int row) {
+    if (valid >= 64)
+        expand_full(rowp, wv, hh, row);
+    else
+        expand_part(rowp, wv, valid, hh, row);
+}
+
 // The work of one CTA: units u = blockIdx.x + n gridDim.x; unit u is sample
 // u / nhalf, row blocks h = u % nhalf and nb - 1 - h (one block when equal).
 // Within a unit the blocks are items; item i has the tiles (i, jb), jb >= i.
-// The producer's chunk sequence per item: A chunks kc = 0..nc-1 of block i,
-// then B chunks kc of blocks jb = i+1..nb-1 (tile (i, i) takes B = A).
-struct Cursor {
-    int u, sidx, h, item, i, jb, kc;
+// The producers' block sequence per item: the A block i, then the B blocks
+// jb = i+1..nb-1 (tile (i, i) takes B = A).
+struct Blk {
+    int u, sidx, h, item, i, jb;
     bool valid;
 };
 
 __device__ __forceinline__ int item_block(int h, int item, int nb) { return item ? nb - 1 - h : h; }
 __device__ __forceinline__ int unit_items(int h, int nb) { return nb - 1 - h != h ? 2 : 1; }
 
-__device__ __forceinline__ void cursor_unit(Cursor &c, int nunits, int nhalf) {
+__device__ __forceinline__ void blk_unit(Blk &c, int nunits, int nhalf) {
     c.valid = c.u < nunits;
     c.sidx = c.u / nhalf;
     c.h = c.u - c.sidx * nhalf;
     c.item = 0;
     c.i = c.h;
     c.jb = c.h;
-    c.kc = 0;
 }
 
-__device__ __forceinline__ void cursor_start(Cursor &c, int nunits, int nhalf) {
+__device__ __forceinline__ void blk_first(Blk &c, int nunits, int nhalf) {
     c.u = blockIdx.x;
-    cursor_unit(c, nunits, nhalf);
+    blk_unit(c, nunits, nhalf);
 }
 
-__device__ __forceinline__ void cursor_next(Cursor &c, int nunits, int nhalf, int nb, int nc) {
-    if (++c.kc < nc) return;
-    c.kc = 0;
+__device__ __forceinline__ void blk_next(Blk &c, int nunits, int nhalf, int nb) {
     if (++c.jb < nb) return;
     if (++c.item >= unit_items(c.h, nb)) {
         c.u += gridDim.x;
-        cursor_unit(c, nunits, nhalf);
+        blk_unit(c, nunits, nhalf);
         return;
     }
     c.i = item_block(c.h, c.item, nb);
     c.jb = c.i;
+}
+
+// Bit words of thread (row, hh) in a block: w[kc] = word 2 kc + hh of row
+// jb * 128 + row, 0 outside the lattice and past L_tau.
+__device__ __forceinline__ void load_blk(const Blk &c, const uint64_t *__restrict__ P, int Lt, int nwx, int nc, int row,
+                                         int hh, uint64_t (&w)[kMaxNc]) {
+    const int t = c.jb * kTile + row;
+    const bool in = c.valid && t < Lt;
+    const uint64_t *src = P + ((size_t)(c.valid ? c.sidx : 0) * Lt + (t < Lt ? t : 0)) * nwx + hh;
+#pragma unroll
+    for (int kc = 0; kc < kMaxNc; ++kc)
+        if (kc < nc) w[kc] = (in && 2 * kc + hh < nwx) ? __ldg(src + 2 * kc) : 0ull;
 }
 
 // FP32 accumulator holding an integer |x| < 2^22 -> int32 with one add: in
@@ -169,7 +218,7 @@ __device__ __forceinline__ int exact_f32_to_int(uint32_t bits) {
 
 // P: [sample][Ltau][nwx] transposed bits of the batch (sample = (pair, r, bit)).
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int *status) {
+    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int nabuf, int *status) {
     extern __shared__ __align__(16) uint8_t dyn_raw[];
     uint8_t *dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
     __shared__ Ctl ctl;
@@ -178,22 +227,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int nc = (L2 + kChunk - 1) / kChunk;
     const int nunits = nsamples * nhalf;
     uint8_t *sA = dyn;
-    uint8_t *sB = sA + (size_t)nc * kChunkBytes;
-    uint64_t *ring = reinterpret_cast<uint64_t *>(sB + (size_t)nstages * kChunkBytes);  // [depth][128 rows][2 words]
-    int *binC = reinterpret_cast<int *>(ring + kBitsDepth * kTile * 2);
+    uint8_t *sB = sA + (size_t)nabuf * nc * kChunkBytes;  // A buffers, then the B stages
+    int *binC = reinterpret_cast<int *>(sB + (size_t)nstages * kChunkBytes);
     unsigned *binQ = reinterpret_cast<unsigned *>(binC + nl);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         for (int s = 0; s < kMaxStages; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.bfull[s])), "r"(kProducers));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.bfull[s])), "r"(kProducerWarps));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.bempty[s])));
         }
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.afull)), "r"(kProducers));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.aempty)));
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.afull[b])), "r"(kProducerWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.aempty[b])));
+        }
         for (int a = 0; a < 2; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.accfull[a])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.accempty[a])), "r"(kEpilogue));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.accempty[a])), "r"(kEpilogueWarps));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.done)));
         asm volatile("fence.mbarrier_init.release.cluster;\n");
@@ -214,84 +264,54 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < kProducers / 32) {
         // ------------------------------------------------------------ producers
-        // thread (row, hh): sites 64 hh .. 64 hh + 63 of each chunk of the row
+        // thread (row, hh): sites 64 hh .. 64 hh + 63 of every 128-site chunk of
+        // a tile row; the bit words of the next block are loaded into registers
+        // while the current block is expanded
         const int row = tid >> 1, hh = tid & 1;
-        Cursor fetch, use;
-        cursor_start(fetch, nunits, nhalf);
-        use = fetch;
-        auto issue = [&](int slot) {
-            if (fetch.valid && !*(volatile int *)&ctl.abort) {
-                const int t = fetch.jb * kTile + row;
-                const int wd = 2 * fetch.kc + hh;
-                const uint64_t *src = P + ((size_t)fetch.sidx * Lt + (t < Lt ? t : Lt - 1)) * nwx + (wd < nwx ? wd : 0);
-                cp_async8(ring + ((size_t)slot * kTile + row) * 2 + hh, src, (t < Lt && wd < nwx) ? 8 : 0);
-            }
-            asm volatile("cp.async.commit_group;\n" ::: "memory");
-            if (fetch.valid) cursor_next(fetch, nunits, nhalf, nb, nc);
-        };
-        for (int d = 0; d < kBitsDepth; ++d) issue(d);
+        Blk cur, nxt;
+        blk_first(cur, nunits, nhalf);
+        uint64_t wc[kMaxNc], wn[kMaxNc];
+        load_blk(cur, P, Lt, nwx, nc, row, hh, wc);
         // aempty / bempty[s] parities: the first use of a buffer waits for the
         // phase before the first (complete at initialisation)
-        uint32_t a_par = 1u, b_par = 1u;
-        int s = 0;
-        for (uint32_t q = 0; use.valid; ++q) {
-            const int slot = (int)(q & (kBitsDepth - 1));
-            asm volatile("cp.async.wait_group %0;\n" ::"n"(kBitsDepth - 1) : "memory");
-            const uint64_t wv = ring[((size_t)slot * kTile + row) * 2 + hh];
-            const bool isA = use.jb == use.i;
-            uint8_t *dst;
-            bool ok = true;
-            if (isA) {
-                if (use.kc == 0) ok = mbar_wait(&ctl.aempty, a_par, &ctl.abort);
-                dst = sA + (size_t)use.kc * kChunkBytes;
-            } else {
-                ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort);
-                dst = sB + (size_t)s * kChunkBytes;
-            }
-            if (ok) {
-                const int t = use.jb * kTile + row;
-                // sites of this thread's 64 that lie inside the lattice (0 past L_tau)
-                const int valid = t < Lt ? L2 - use.kc * kChunk - 64 * hh : 0;
-                uint8_t *rowp = dst + row * kChunk;
-                // output words 8 e + j (e = half of the 64-bit word, j = 0..7)
-                // fill granules 4 hh + 2 e + (j >> 2)
+        uint32_t a_par = 3u, b_par = 1u;  // a_par: bit b = parity of A buffer b
+        int s = 0, ab = 0;
+        while (cur.valid) {
+            nxt = cur;
+            blk_next(nxt, nunits, nhalf, nb);
+            load_blk(nxt, P, Lt, nwx, nc, row, hh, wn);
+            const int t = cur.jb * kTile + row;
+            const bool isA = cur.jb == cur.i;  // the A block of an item
+            uint8_t *abuf = sA + (size_t)ab * nc * kChunkBytes + row * kChunk;
 #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const uint32_t b = (uint32_t)(wv >> (32 * e));
-                    uint32_t o[8];
-#pragma unroll
-                    for (int jj = 0; jj < 8; ++jj) o[jj] = spread_e4m3(b, jj);
-                    if (valid < 64) {  // sites 32 e + 8 k + j of this thread's 64
-                        const int v32 = valid - 32 * e;
-                        const uint32_t vm = v32 >= 32 ? 0xFFFFFFFFu : (v32 <= 0 ? 0u : (1u << v32) - 1u);
-#pragma unroll
-                        for (int jj = 0; jj < 8; ++jj) o[jj] &= spread_mask(vm, jj);
-                    }
-#pragma unroll
-                    for (int hq = 0; hq < 2; ++hq) {
-                        const int gr = 4 * hh + 2 * e + hq;
-                        *reinterpret_cast<uint4 *>(rowp + ((gr ^ (row & 7)) << 4)) =
-                            make_uint4(o[4 * hq], o[4 * hq + 1], o[4 * hq + 2], o[4 * hq + 3]);
+            for (int kc = 0; kc < kMaxNc; ++kc) {
+                if (kc < nc) {
+                    bool ok = true;
+                    if (!isA)
+                        ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort);
+                    else if (kc == 0)
+                        ok = mbar_wait(&ctl.aempty[ab], (a_par >> ab) & 1u, &ctl.abort);
+                    uint8_t *rowp = isA ? abuf + (size_t)kc * kChunkBytes : sB + (size_t)s * kChunkBytes + row * kChunk;
+                    if (ok) expand_word(rowp, wc[kc], t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
+                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                    __syncwarp();  // the warp's rows are written: one arrival per warp
+                    if (!isA) {
+                        if (lane == 0) mbar_arrive(&ctl.bfull[s]);
+                        if (++s == nstages) {
+                            s = 0;
+                            b_par ^= 1u;
+                        }
+                    } else if (kc == nc - 1) {
+                        if (lane == 0) mbar_arrive(&ctl.afull[ab]);
+                        a_par ^= 1u << ab;
+                        if (++ab == nabuf) ab = 0;
                     }
                 }
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             }
-            if (isA) {
-                if (use.kc == nc - 1) {
-                    mbar_arrive(&ctl.afull);
-                    a_par ^= 1u;
-                }
-            } else {
-                mbar_arrive(&ctl.bfull[s]);
-                if (++s == nstages) {
-                    s = 0;
-                    b_par ^= 1u;
-                }
-            }
-            issue(slot);
-            cursor_next(use, nunits, nhalf, nb, nc);
+#pragma unroll
+            for (int kc = 0; kc < kMaxNc; ++kc) wc[kc] = wn[kc];
+            cur = nxt;
         }
-        asm volatile("cp.async.wait_all;\n" ::: "memory");
     } else if (warp < kMmaWarp) {
         // ------------------------------------------------------------- epilogue
         const int etid = tid - kProducers;
@@ -332,21 +352,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
                         // the accumulator is free for the tile after next
                         asm volatile("tcgen05.fence::before_thread_sync;\n");
-                        mbar_arrive(&ctl.accempty[a]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&ctl.accempty[a]);
                         const int o0 = obase + cbase - m;  // offset of column q is o0 + q
-                        if (full && cls == 0 && jb != i) {
+                        if (full && cls != 2 && jb != i) {
+                            // every element of the tile folds the same way:
+                            // lag o0 + q (all o < L_tau/2) or L_tau - o0 - q
+                            const int base = cls == 0 ? o0 : Lt - o0, step = cls == 0 ? 1 : -1;
+                            const int sgn = cls == 0 ? 1 : whigh;
+                            int *bc = binC + base;
+                            unsigned *bq = binQ + base;
 #pragma unroll
                             for (int q = 0; q < 64; ++q) {
                                 const int gv = exact_f32_to_int(v[q]);
-                                atomicAdd(&binC[o0 + q], gv);
-                                atomicAdd(&binQ[o0 + q], (unsigned)(gv * gv));
-                            }
-                        } else if (full && cls == 1) {
-#pragma unroll
-                            for (int q = 0; q < 64; ++q) {
-                                const int gv = exact_f32_to_int(v[q]);
-                                atomicAdd(&binC[Lt - o0 - q], whigh * gv);
-                                atomicAdd(&binQ[Lt - o0 - q], (unsigned)(gv * gv));
+                                atomicAdd(bc + step * q, sgn * gv);
+                                atomicAdd(bq + step * q, (unsigned)(gv * gv));
                             }
                         } else if (t1 < Lt) {
 #pragma unroll
@@ -370,7 +390,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     } else {
                         asm volatile("tcgen05.fence::before_thread_sync;\n");
-                        mbar_arrive(&ctl.accempty[a]);
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&ctl.accempty[a]);
                     }
                 }
             }
@@ -402,20 +423,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------------ MMA
         const uint32_t idesc = idesc_e4m3_128x128();
         uint32_t a_par = 0u, b_par = 0u, n_t = 0;
-        int bs = 0;
+        int bs = 0, ab = 0;
         bool issued = false;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
             const int h = u % nhalf;
             for (int item = 0; item < unit_items(h, nb); ++item) {
                 const int i = item_block(h, item, nb);
-                const bool a_ok = mbar_wait(&ctl.afull, a_par, &ctl.abort);
+                const bool a_ok = mbar_wait(&ctl.afull[ab], (a_par >> ab) & 1u, &ctl.abort);
+                const uint8_t *sAb = sA + (size_t)ab * nc * kChunkBytes;
                 asm volatile("tcgen05.fence::after_thread_sync;\n");
                 for (int jb = i; jb < nb; ++jb, ++n_t) {
                     const int a = (int)(n_t & 1u);
                     bool ok = a_ok && mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort);
                     asm volatile("tcgen05.fence::after_thread_sync;\n");
                     for (int kc = 0; kc < nc; ++kc) {
-                        const uint32_t abase = smem_u32(sA + (size_t)kc * kChunkBytes);
+                        const uint32_t abase = smem_u32(sAb + (size_t)kc * kChunkBytes);
                         uint32_t bbase = abase;
                         if (jb != i) {
                             ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort) && ok;
@@ -447,9 +469,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (lane == 0) mma_commit(&ctl.accfull[a]);
                     __syncwarp();
                 }
-                if (lane == 0) mma_commit(&ctl.aempty);
+                if (lane == 0) mma_commit(&ctl.aempty[ab]);
                 __syncwarp();
-                a_par ^= 1u;
+                a_par ^= 1u << ab;
+                if (++ab == nabuf) ab = 0;
             }
         }
         // every MMA issued has completed before the tensor memory is released
@@ -477,28 +500,35 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 namespace {
 
-size_t gram_tc_smem_bytes(const Group &g, int nstages) {
+size_t gram_tc_smem_bytes(const Group &g, int nstages, int nabuf) {
     const int nc = (g.L * g.L + kChunk - 1) / kChunk;
-    return 1024 + (size_t)(nc + nstages) * kChunkBytes + (size_t)kBitsDepth * kTile * 2 * sizeof(uint64_t) +
-           2 * sizeof(int) * (size_t)g.nlag;
+    return 1024 + (size_t)(nabuf * nc + nstages) * kChunkBytes + 2 * sizeof(int) * (size_t)g.nlag;
 }
 
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = 227 * 1024 - 256;  // dynamic + the static control block
 
-int gram_tc_stages(const Group &g) {
-    for (int s = kMaxStages; s >= 2; --s)
-        if (gram_tc_smem_bytes(g, s) <= kSmemLimit) return s;
-    return 0;
+// Shared-memory plan: two A buffers (the next row block is expanded while the
+// last tiles of the current one are multiplied) with at least four B stages
+// where that fits, else one A buffer; as many B stages as fit, up to six.
+struct TcPlan {
+    int nstages, nabuf;
+};
+
+TcPlan gram_tc_plan(const Group &g) {
+    for (int nabuf = 2; nabuf >= 1; --nabuf)
+        for (int s = kMaxStages; s >= (nabuf == 2 ? 4 : 2); --s)
+            if (gram_tc_smem_bytes(g, s, nabuf) <= kSmemLimit) return {s, nabuf};
+    return {0, 0};
 }
 
 }  // namespace
 
-bool gram_tc_fits(const Group &g) { return gram_tc_stages(g) >= 2; }
+bool gram_tc_fits(const Group &g) { return gram_tc_plan(g).nstages >= 2; }
 
 cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st) {
-    const int nstages = gram_tc_stages(g);
-    if (nstages < 2) return cudaErrorInvalidValue;
-    const size_t sm = gram_tc_smem_bytes(g, nstages);
+    const TcPlan plan = gram_tc_plan(g);
+    if (plan.nstages < 2) return cudaErrorInvalidValue;
+    const size_t sm = gram_tc_smem_bytes(g, plan.nstages, plan.nabuf);
     cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int dev = 0, nsm = 0;
@@ -510,7 +540,7 @@ cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P
     const long long nunits = (long long)nsamples * ((nb + 1) / 2);
     const int grid = (int)(nunits < nsm ? nunits : nsm);
     count_launches(1);
-    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, nstages, status);
+    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, plan.nstages, plan.nabuf, status);
     return cudaGetLastError();
 }
 
