@@ -83,7 +83,17 @@ def _case_step(Q, W):
     return ctx
 
 
-PROFILE_CASES = {"sweep": _case_sweep, "measure": _case_measure, "step": _case_step}
+def _case_tempering(Q, W):
+    # L=24, L_tau=2048, 128 samples, 1 replica, 32 k (0.60 GB): energies and swaps of two tempering steps
+    ctx = Q.Context([Q.Shape(24, 2048, 128, 1, 32, Q.HEATBATH, Q.PBC)])
+    ctx.qsg_init_samples(3, [W.uniform_ladder(0.22, 0.36, 32)])
+    for _ in range(2):
+        ctx.qsg_sweep(1)
+        ctx.qsg_tempering_swap()
+    return ctx
+
+
+PROFILE_CASES = {"sweep": _case_sweep, "measure": _case_measure, "step": _case_step, "tempering": _case_tempering}
 
 
 def run_profile_case(name):
