@@ -5,8 +5,8 @@
 namespace qsg {
 
 constexpr int kEnergyPlanes = 16;
-constexpr int kEnergyRun = 240;  // tau planes per thread (a multiple of kFlush)
-constexpr int kFlush = 5;       // planes between flushes of the 4-bit accumulator (5 * 3 <= 15)
+constexpr int kEnergyGroup = 10;  // planes per carry-save group: 3 * 10 <= 31 fits five bit planes
+constexpr int kEnergyRun = 120;   // tau planes per block (a multiple of the group)
 
 // a += b for two bitsliced counters of kEnergyPlanes planes (ripple carry)
 __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const uint64_t (&b)[kEnergyPlanes]) {
@@ -21,13 +21,15 @@ __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const
 
 // U[slot][b] += number of unsatisfied bonds (J S S' = -1) among the three
 // forward bonds (+x, +y, +tau) of every site; each bond is counted once and
-// E = -(3N - 2U) is the action of Eq. (Trotter-action).  One thread per site
-// of a plane walks kEnergyRun planes with coalesced loads.  The three bond
-// words of a site go through a full adder into a 4-bit carry-save
-// accumulator (ones, twos, fours, eights), which is added into the 8-plane
-// per-thread counter every kFlush planes; the warp then sums its counters
-// with shuffles and one lane turns them into per-sample integers.
-__global__ void __launch_bounds__(256) k_energy(Group g) {
+// E = -(3N - 2U) is the action of Eq. (Trotter-action).  A block covers the
+// sites [xy0, xy0 + blockDim.x) of one slot over kEnergyRun planes, one thread
+// per site walking the planes with coalesced loads; the word of the next
+// plane, loaded as the +tau neighbour, is the next plane's own word.  The
+// three bond words of a site go through a full adder into a 5-bit carry-save
+// accumulator, added into the 10-plane per-thread counter once per
+// kEnergyGroup planes; the warp then sums its counters with shuffles and one
+// lane turns them into per-sample integers.
+__global__ void __launch_bounds__(512) k_energy(Group g) {
     __shared__ int cnt[64];
     const int s = blockIdx.y;
     const int L = g.L, L2 = L * L, Lt = g.Ltau;
@@ -38,48 +40,53 @@ __global__ void __launch_bounds__(256) k_energy(Group g) {
     uint64_t c[kEnergyPlanes];
 #pragma unroll
     for (int p = 0; p < kEnergyPlanes; ++p) c[p] = 0;
-    const int xy = blockIdx.x * blockDim.x + threadIdx.x;  // site within a plane (grid.x covers L^2)
+    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
     const int t0 = blockIdx.z * kEnergyRun, t1 = min(t0 + kEnergyRun, Lt);
     if (xy < L2) {
         const int y = xy / L, x = xy - y * L;
         const int xr = y * L + (x + 1 == L ? 0 : x + 1), yu = (y + 1 == L ? 0 : y + 1) * L + x;
         const uint64_t jx = g.Jx[(size_t)w * L2 + xy], jy = g.Jy[(size_t)w * L2 + xy];
-        for (int tb = t0; tb < t1; tb += kFlush) {
-            uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0;
+        const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
+        uint64_t v = __ldg(S + (size_t)t0 * L2 + xy);
+        for (int tb = t0; tb < t1; tb += kEnergyGroup) {
+            uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0, o16 = 0;
 #pragma unroll
-            for (int k = 0; k < kFlush; ++k) {
+            for (int k = 0; k < kEnergyGroup; ++k) {
                 const int t = tb + k;
                 if (t < t1) {
                     const uint64_t *P = S + (size_t)t * L2;
-                    const int tn = t + 1 == Lt ? 0 : t + 1;
-                    const uint64_t v = __ldg(P + xy);
-                    const uint64_t vt = __ldg(S + (size_t)tn * L2 + xy);
-                    const uint64_t ft = (g.boundary == 1 && t == Lt - 1) ? ~0ull : 0ull;
-                    const uint64_t ux = v ^ __ldg(P + xr) ^ jx, uy = v ^ __ldg(P + yu) ^ jy, ut = v ^ vt ^ ft;
+                    const bool wrap = t + 1 == Lt;
+                    const uint64_t vt = __ldg(S + (size_t)(wrap ? 0 : t + 1) * L2 + xy);
+                    const uint64_t ux = v ^ __ldg(P + xr) ^ jx, uy = v ^ __ldg(P + yu) ^ jy;
+                    const uint64_t ut = v ^ vt ^ (wrap ? apbc : 0ull);
                     const uint64_t sum = ux ^ uy ^ ut, car = (ux & uy) | (ut & (ux ^ uy));
+                    // (o16 o8 o4 o2 o1) += sum + 2 car
                     const uint64_t h1 = o1 & sum;
                     o1 ^= sum;
                     const uint64_t h2 = (o2 & car) | (h1 & (o2 ^ car));
                     o2 ^= car ^ h1;
                     const uint64_t h4 = o4 & h2;
                     o4 ^= h2;
-                    o8 ^= h4;  // at most 5 * 3 = 15 per position: no carry out of o8
+                    const uint64_t h8 = o8 & h4;
+                    o8 ^= h4;
+                    o16 ^= h8;  // at most 3 * 10 = 30 per position: no carry out of o16
+                    v = vt;
                 }
             }
-            // c += (o8 o4 o2 o1): ripple over the low planes (a thread counts at
-            // most 3 * kEnergyRun < 2^10 per position)
+            // c += (o16 o8 o4 o2 o1): ripple over the low planes (a thread counts
+            // at most 3 * kEnergyRun < 2^9 per position)
             uint64_t carry = 0;
-            const uint64_t in[4] = {o1, o2, o4, o8};
+            const uint64_t in[5] = {o1, o2, o4, o8, o16};
 #pragma unroll
             for (int p = 0; p < 10; ++p) {
-                const uint64_t b = p < 4 ? in[p] : 0ull;
+                const uint64_t b = p < 5 ? in[p] : 0ull;
                 const uint64_t sp = c[p] ^ b ^ carry;
                 carry = (c[p] & b) | (carry & (c[p] ^ b));
                 c[p] = sp;
             }
         }
     }
-    // warp sum of the bitsliced counters (at most 32 * 3 * kEnergyRun < 2^16)
+    // warp sum of the bitsliced counters (at most 32 * 3 * kEnergyRun < 2^14)
     for (int o = 16; o > 0; o >>= 1) {
         uint64_t other[kEnergyPlanes];
 #pragma unroll
@@ -107,9 +114,11 @@ __global__ void __launch_bounds__(256) k_energy(Group g) {
 cudaError_t launch_energy(const Group &g, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g.U, 0, sizeof(int32_t) * (size_t)g.nslots * 64, st);
     if (e != cudaSuccess) return e;
+    // blocks of at most 512 threads tiling the plane with the fewest idle threads
     const int L2 = g.L * g.L;
-    const int threads = L2 >= 256 ? 256 : ((L2 + 31) / 32) * 32;
-    dim3 grid((L2 + threads - 1) / threads, g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
+    const int nblk = (L2 + 511) / 512;
+    const int threads = ((L2 + nblk - 1) / nblk + 31) / 32 * 32;
+    dim3 grid(nblk, g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
     count_launches(1);
     k_energy<<<grid, threads, 0, st>>>(g);
     return cudaGetLastError();
