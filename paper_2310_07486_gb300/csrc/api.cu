@@ -518,40 +518,32 @@ qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *
     if (!ctx->initialised) return QSG_ERR_STATE;
     const Group &g = ctx->groups[group];
     QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
-    const size_t nc = (size_t)g.R * g.W * 64 * g.K * g.nlag;
-    const size_t np = (size_t)g.W * 64 * g.K;
-    std::vector<double> hc(nc), hq(nc), hp(np);
-    std::vector<long long> rc, rq, rp;
-    QSG_CUDA(ctx, cudaMemcpyAsync(hc.data(), g.outC, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-    QSG_CUDA(ctx, cudaMemcpyAsync(hq.data(), g.outQ, sizeof(double) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-    QSG_CUDA(ctx, cudaMemcpyAsync(hp.data(), g.outP, sizeof(double) * np, cudaMemcpyDeviceToHost, ctx->stream));
-    if (raw) {
-        rc.resize(nc);
-        rq.resize(nc);
-        rp.resize(np);
-        QSG_CUDA(ctx, cudaMemcpyAsync(rc.data(), g.Cacc, sizeof(long long) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-        QSG_CUDA(ctx, cudaMemcpyAsync(rq.data(), g.Qacc, sizeof(long long) * nc, cudaMemcpyDeviceToHost, ctx->stream));
-        QSG_CUDA(ctx, cudaMemcpyAsync(rp.data(), g.Pacc, sizeof(long long) * np, cudaMemcpyDeviceToHost, ctx->stream));
-    }
-    qsg_status s = check_device_flag(ctx);
-    if (s != QSG_OK) return s;
+    // device layout [R][W*64][K][nl]; the host keeps the first n_samples of the
+    // W*64 sample bits, so every replica is one contiguous block on both sides
+    // and the copies go straight into the caller's buffers (at DMA speed when
+    // they are page-locked)
     const int S = g.n_samples, Sp = g.W * 64, K = g.K, nl = g.nlag;
-    const size_t outc = (size_t)g.R * S * K * nl;
-    for (int r = 0; r < g.R; ++r)
-        for (int b = 0; b < S; ++b) {
-            const size_t src = (((size_t)r * Sp + b) * K) * nl, dst = (((size_t)r * S + b) * K) * nl;
-            if (C) std::memcpy(C + dst, hc.data() + src, sizeof(double) * K * nl);
-            if (Q2) std::memcpy(Q2 + dst, hq.data() + src, sizeof(double) * K * nl);
-            if (raw) {
-                std::memcpy(raw + dst, rc.data() + src, sizeof(long long) * K * nl);
-                std::memcpy(raw + outc + dst, rq.data() + src, sizeof(long long) * K * nl);
-            }
+    const size_t blk = (size_t)S * K * nl, pitch = (size_t)Sp * K * nl, outc = (size_t)g.R * blk;
+    for (int r = 0; r < g.R; ++r) {
+        if (C)
+            QSG_CUDA(ctx, cudaMemcpyAsync(C + r * blk, g.outC + r * pitch, sizeof(double) * blk, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+        if (Q2)
+            QSG_CUDA(ctx, cudaMemcpyAsync(Q2 + r * blk, g.outQ + r * pitch, sizeof(double) * blk,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        if (raw) {
+            QSG_CUDA(ctx, cudaMemcpyAsync(raw + r * blk, g.Cacc + r * pitch, sizeof(long long) * blk,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+            QSG_CUDA(ctx, cudaMemcpyAsync(raw + outc + r * blk, g.Qacc + r * pitch, sizeof(long long) * blk,
+                                          cudaMemcpyDeviceToHost, ctx->stream));
         }
-    for (int b = 0; b < S; ++b) {
-        if (q2) std::memcpy(q2 + (size_t)b * K, hp.data() + (size_t)b * K, sizeof(double) * K);
-        if (raw) std::memcpy(raw + 2 * outc + (size_t)b * K, rp.data() + (size_t)b * K, sizeof(long long) * K);
     }
-    return QSG_OK;
+    if (q2)
+        QSG_CUDA(ctx, cudaMemcpyAsync(q2, g.outP, sizeof(double) * (size_t)S * K, cudaMemcpyDeviceToHost, ctx->stream));
+    if (raw)
+        QSG_CUDA(ctx, cudaMemcpyAsync(raw + 2 * outc, g.Pacc, sizeof(long long) * (size_t)S * K, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    return check_device_flag(ctx);
 }
 
 qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, double *per_k, int64_t *raw) {

@@ -262,12 +262,33 @@ class Context:
     def qsg_measure_correlators(self):
         self._check(self.lib.qsg_measure_correlators(self.h), "qsg_measure_correlators")
 
-    def qsg_read_correlators(self, group=0, raw=False):
+    def correlator_buffers(self, group=0, pinned=False):
+        """Host arrays C, Q2 [R][n_samples][K][L_tau/2+1] and q2 [n_samples][K]
+        for qsg_read_correlators(out=...); page-locked (torch pin_memory) when
+        pinned, so that the device copies run at DMA speed."""
         s = self.shapes[group]
         shp = (s.n_replicas, s.n_samples, s.n_k, s.n_lag)
-        C = np.zeros(shp)
-        Q = np.zeros(shp)
-        P = np.zeros((s.n_samples, s.n_k))
+        if pinned:
+            import torch
+            mk = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+        else:
+            mk = lambda shape: np.empty(shape)
+        return dict(C=mk(shp), Q2=mk(shp), q2=mk((s.n_samples, s.n_k)))
+
+    def qsg_read_correlators(self, group=0, raw=False, out=None):
+        """C, Q2 and q2 of one group; `out` (from correlator_buffers) receives
+        them in place instead of new arrays."""
+        s = self.shapes[group]
+        shp = (s.n_replicas, s.n_samples, s.n_k, s.n_lag)
+        if out is None:
+            C = np.zeros(shp)
+            Q = np.zeros(shp)
+            P = np.zeros((s.n_samples, s.n_k))
+        else:
+            C, Q, P = out["C"], out["Q2"], out["q2"]
+            for a, want in ((C, shp), (Q, shp), (P, (s.n_samples, s.n_k))):
+                if a.shape != want or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("qsg_read_correlators: out arrays must be C-contiguous float64 of shape %s" % (want,))
         nc = int(np.prod(shp))
         R = np.zeros(2 * nc + s.n_samples * s.n_k, dtype=np.int64) if raw else None
         self._check(self.lib.qsg_read_correlators(self.h, group, _ptr(C), _ptr(Q), _ptr(P),

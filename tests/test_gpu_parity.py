@@ -455,3 +455,25 @@ def test_many_ladder_pairs_in_one_measurement_batch():
         assert np.array_equal(got["C_raw"][:, b], ref["C_raw"][:, 0])
         assert np.array_equal(got["Q2_raw"][:, b], ref["Q2_raw"][:, 0])
         assert np.array_equal(got["q2_raw"][b], ref["q2_raw"][0])
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_correlator_readback_into_caller_buffers(pinned):
+    """Reading into caller-owned (page-locked or pageable) buffers gives the
+    same arrays as fresh ones; 70 samples leave padding bits in the second
+    word, so every replica block is taken at its own offset."""
+    shape = Q.Shape(6, 32, 70, 3, 2, Q.HEATBATH, Q.PBC)
+    ctx, orc = _pair(shape, np.array([0.27, 0.31]), seed=9)
+    ctx.qsg_sweep(2)
+    orc.sweep(2)
+    ctx.qsg_measure_correlators()
+    orc.measure()
+    ref = ctx.qsg_read_correlators(raw=True)
+    _check_corr(ref, orc.read())
+    out = ctx.correlator_buffers(pinned=pinned)
+    for a in out.values():
+        a.fill(np.nan)
+    got = ctx.qsg_read_correlators(out=out)
+    for k in ("C", "Q2", "q2"):
+        assert got[k] is out[k]
+        assert np.array_equal(got[k], ref[k])
