@@ -13,78 +13,153 @@
 // the sites of column (row) c, |Q(p)|^2 = sum_d cos(2 pi d / L) G[d] where
 // G[d] = sum_c n_c n_{c+d}; the kernel accumulates the integer sums G[d]
 // (folded d ~ L - d) and the finish applies the cosines, so the accumulation
-// is exact.
+// is exact.  With a_c the number of sites of column c where the two replicas
+// differ (n_c = L - 2 a_c) and A = sum_c a_c,
+//   sum_c n_c n_{c+d} = L^3 - 4 L A + 4 sum_c a_c a_{c+d},
+// and the last sum is a dot product of byte vectors (four columns per
+// __dp4a); the column counts come from a bitsliced vertical add of the L row
+// words of the slice.
 //
 // Input: the transposed scratch of the correlator pass ([pair][r][bit][tau]
 // [nwx] x-packed slices, bit n = y L + x of word n / 64).  One block per
 // (ladder pair of the batch, sample bit), one thread per slice.
+#include <type_traits>
+
 #include "qsg_launch.h"
 
 namespace qsg {
 
 constexpr int kMaxTripleR = 8;  // three-replica terms for 3 <= R <= 8
 
-// Column masks of the x-packed slice: bit i of word w is site 64 w + i.
+__host__ __device__ constexpr int bit_length(int n) { return n == 0 ? 0 : 1 + bit_length(n >> 1); }
+
+// Sizes for lattice side L: NW words per slice, NP packed byte words per
+// count vector (4 columns per word, zero beyond L), NPL bit planes of a count
+// (<= L), ND words of the doubled cyclic copy read by the shifted windows.
 template <int L>
-struct ColumnMasks {
+struct OtSize {
     static constexpr int NW = (L * L + 63) / 64;
-    uint64_t m[L][NW];
-    constexpr ColumnMasks() : m() {
-        for (int c = 0; c < L; ++c)
-            for (int w = 0; w < NW; ++w) {
-                uint64_t v = 0;
-                for (int i = 0; i < 64; ++i) {
-                    const int n = 64 * w + i;
-                    if (n < L * L && n % L == c) v |= 1ull << i;
-                }
-                m[c][w] = v;
-            }
-    }
+    static constexpr int NP = (L + 3) / 4;
+    static constexpr int NPL = bit_length(L);
+    static constexpr int ND = ((L - 1) + 4 * (NP - 1)) / 4 + 2;
 };
 
-// Overlap sums of one replica pair at one slice: ny[r] over row r, nx[c] over
-// column c (each L - 2 * #{sites with opposite spins}).
+// Pack four small non-negative ints into bytes 0..3.
+__device__ __forceinline__ uint32_t pack_bytes(uint32_t b0, uint32_t b1, uint32_t b2, uint32_t b3) {
+    return __byte_perm(__byte_perm(b0, b1, 0x0040), __byte_perm(b2, b3, 0x0040), 0x5410);
+}
+
+// Difference counts of one replica pair at one slice: ca (columns) and cb
+// (rows) as byte vectors [NP] (byte k of word w = count of column / row
+// 4 w + k), and the total A = number of sites where the replicas differ.
 template <int L>
-__device__ __forceinline__ void overlap_sums(const uint64_t *__restrict__ A, const uint64_t *__restrict__ B,
-                                             int (&nx)[L], int (&ny)[L]) {
-    constexpr int NW = (L * L + 63) / 64;
-    constexpr ColumnMasks<L> cm{};
+__device__ __forceinline__ void diff_counts(const uint64_t *__restrict__ X, const uint64_t *__restrict__ Y,
+                                            uint32_t (&ca)[OtSize<L>::NP], uint32_t (&cb)[OtSize<L>::NP], int &A) {
+    constexpr int NW = OtSize<L>::NW, NP = OtSize<L>::NP, NPL = OtSize<L>::NPL;
     uint64_t o[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) o[q] = A[q] ^ B[q];
+    for (int q = 0; q < NW; ++q) o[q] = X[q] ^ Y[q];
+    // rows (bits r L .. r L + L - 1), their counts, and the vertical bitsliced
+    // sum of the rows: bit c of plane j is bit j of column c's count; after
+    // row r a count is at most r + 1, which bounds the carry chain
+    uint32_t P[NPL];
+#pragma unroll
+    for (int j = 0; j < NPL; ++j) P[j] = 0u;
+    uint32_t rb[4 * NP];
+    A = 0;
 #pragma unroll
     for (int r = 0; r < L; ++r) {
-        constexpr uint64_t mask = L == 64 ? ~0ull : ((1ull << L) - 1);
+        constexpr uint64_t mask = (L == 64) ? ~0ull : ((1ull << L) - 1);
         const int off = r * L, q = off >> 6, sh = off & 63;
         uint64_t f = o[q] >> sh;
         if (sh + L > 64) f |= o[q + 1] << (64 - sh);
-        ny[r] = L - 2 * __popcll(f & mask);
+        const uint32_t row = (uint32_t)(f & mask);
+        rb[r] = (uint32_t)__popc(row);
+        A += (int)rb[r];
+        uint32_t carry = row;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j)
+            if (j < bit_length(r + 1)) {
+                const uint32_t t = P[j] & carry;
+                P[j] ^= carry;
+                carry = t;
+            }
     }
 #pragma unroll
-    for (int c = 0; c < L; ++c) {
-        int cnt = 0;
+    for (int r = L; r < 4 * NP; ++r) rb[r] = 0u;
 #pragma unroll
-        for (int q = 0; q < NW; ++q)
-            if (cm.m[c][q]) cnt += __popcll(o[q] & cm.m[c][q]);
-        nx[c] = L - 2 * cnt;
+    for (int w = 0; w < NP; ++w) {
+        cb[w] = pack_bytes(rb[4 * w], rb[4 * w + 1], rb[4 * w + 2], rb[4 * w + 3]);
+        // bits 4w .. 4w+3 of every plane spread to the low bit of bytes 0..3
+        uint32_t v = 0u;
+#pragma unroll
+        for (int j = 0; j < NPL; ++j) v |= (((P[j] >> (4 * w)) & 0xFu) * 0x00204081u & 0x01010101u) << j;
+        ca[w] = v;
+    }
+}
+
+// The doubled cyclic copy dd[b] = x[b mod L] of a byte vector x[NP] (bytes
+// beyond L of x are 0); every word takes its four bytes from at most two
+// words of x, chosen at compile time.
+template <int L>
+__device__ __forceinline__ void cyclic_copy(const uint32_t (&x)[OtSize<L>::NP], uint32_t (&dd)[OtSize<L>::ND]) {
+#pragma unroll
+    for (int k = 0; k < OtSize<L>::ND; ++k) {
+        const int c0 = (4 * k) % L;
+        const int wa = c0 / 4;
+        int wb = wa;
+        uint32_t sel = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int c = (4 * k + i) % L, w = c / 4;
+            if (w != wa) wb = w;
+            sel |= (uint32_t)((w == wa ? 0 : 4) + c % 4) << (4 * i);
+        }
+        dd[k] = __byte_perm(x[wa], x[wb], sel);
+    }
+}
+
+// sum_c x[c] y[(c + o) mod L] for byte vectors x (zero beyond L) and the
+// cyclic copy dd of y; o a compile-time offset.
+template <int L, int O>
+__device__ __forceinline__ int cyc_dot(const uint32_t (&x)[OtSize<L>::NP], const uint32_t (&dd)[OtSize<L>::ND]) {
+    unsigned acc = 0u;
+#pragma unroll
+    for (int w = 0; w < OtSize<L>::NP; ++w) {
+        constexpr int sh = O & 3;
+        const int k = (O >> 2) + w;
+        const uint32_t y = sh == 0 ? dd[k] : __byte_perm(dd[k], dd[k + 1], 0x3210u + 0x1111u * sh);
+        acc = __dp4a(x[w], y, acc);
+    }
+    return (int)acc;
+}
+
+// Compile-time loop over d = 0 .. H with the body f(integral_constant<d>).
+template <int D, int H, class F>
+__device__ __forceinline__ void for_d(F &&f) {
+    if constexpr (D <= H) {
+        f(std::integral_constant<int, D>{});
+        for_d<D + 1, H>(f);
     }
 }
 
 template <int L>
 __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint64_t *__restrict__ P, int triples) {
-    constexpr int NW = (L * L + 63) / 64, H = L / 2;
+    constexpr int NW = OtSize<L>::NW, NP = OtSize<L>::NP, ND = OtSize<L>::ND, H = L / 2;
+    constexpr int L3 = L * L * L;
     extern __shared__ __align__(16) unsigned char ot_smem[];
     const int R = g.R, Lt = g.Ltau, bd = blockDim.x, tid = threadIdx.x;
     const int npair = R * (R - 1) / 2;
     const bool do3 = triples && R >= 3 && R <= kMaxTripleR;
     // [pair] per-pair sums of Q^2; [2][L/2+1][thread] the thread's G and F3 sums
     // (kept in shared memory to spare registers); then (triples only)
-    // [pair][dir][c][thread] column/row sums and [pair][thread] overlaps
+    // [pair][dir][word][thread] packed column/row difference counts and
+    // [pair][thread] overlaps
     unsigned long long *ppsh = reinterpret_cast<unsigned long long *>(ot_smem);
     long long *accsh = reinterpret_cast<long long *>(ot_smem + (size_t)npair * 8);
     const size_t o_n = (size_t)npair * 8 + (size_t)2 * (H + 1) * bd * 8;
-    int8_t *nsh = reinterpret_cast<int8_t *>(ot_smem + o_n);
-    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + o_n + (size_t)npair * 2 * L * bd);
+    uint32_t *nsh = reinterpret_cast<uint32_t *>(ot_smem + o_n);
+    int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + o_n + (size_t)npair * 2 * NP * 4 * bd);
     for (int i = tid; i < npair; i += bd) ppsh[i] = 0ull;
 #pragma unroll
     for (int d = 0; d <= H; ++d) {
@@ -103,30 +178,34 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
         int pi = 0;
         for (int ra = 0; ra < R; ++ra)
             for (int rb = ra + 1; rb < R; ++rb, ++pi) {
-                int nx[L], ny[L];
-                overlap_sums<L>(base + (size_t)ra * 64 * plane + (size_t)t * NW,
-                                base + (size_t)rb * 64 * plane + (size_t)t * NW, nx, ny);
-                int q0 = 0;
-#pragma unroll
-                for (int r = 0; r < L; ++r) q0 += ny[r];
+                uint32_t ca[NP], cb[NP];
+                int A;
+                diff_counts<L>(base + (size_t)ra * 64 * plane + (size_t)t * NW,
+                               base + (size_t)rb * 64 * plane + (size_t)t * NW, ca, cb, A);
+                const int q0 = L * L - 2 * A;
                 const unsigned long long q2 = (unsigned long long)(q0 * q0);
                 p2 += (long long)q2;
                 atomicAdd(&ppsh[pi], q2);
                 const unsigned long long q4 = q2 * q2;
                 p4lo += q4 & 0xFFFFFFFFull;
                 p4hi += q4 >> 32;
-#pragma unroll
-                for (int d = 0; d <= H; ++d) {
-                    int s = 0;
-#pragma unroll
-                    for (int c = 0; c < L; ++c) s += nx[c] * nx[(c + d) % L] + ny[c] * ny[(c + d) % L];
-                    accsh[(size_t)d * bd + tid] += (d == 0 || d == H) ? s : 2 * s;  // G[d] = G[L - d]
+                // G[d] = sum_c nx_c nx_{c+d} + ny_c ny_{c+d}
+                //      = 2 L^3 - 8 L A + 4 (sum_c a_c a_{c+d} + sum_r b_r b_{r+d})
+                {
+                    uint32_t dda[ND], ddb[ND];
+                    cyclic_copy<L>(ca, dda);
+                    cyclic_copy<L>(cb, ddb);
+                    for_d<0, H>([&](auto dc) {
+                        constexpr int d = decltype(dc)::value;
+                        const int sv = 2 * L3 - 8 * L * A + 4 * (cyc_dot<L, d>(ca, dda) + cyc_dot<L, d>(cb, ddb));
+                        accsh[(size_t)d * bd + tid] += (d == 0 || d == H) ? sv : 2 * sv;  // G[d] = G[L - d]
+                    });
                 }
                 if (do3) {
 #pragma unroll
-                    for (int c = 0; c < L; ++c) {
-                        nsh[(((size_t)pi * 2 + 0) * L + c) * bd + tid] = (int8_t)nx[c];
-                        nsh[(((size_t)pi * 2 + 1) * L + c) * bd + tid] = (int8_t)ny[c];
+                    for (int w = 0; w < NP; ++w) {
+                        nsh[(((size_t)pi * 2 + 0) * NP + w) * bd + tid] = ca[w];
+                        nsh[(((size_t)pi * 2 + 1) * NP + w) * bd + tid] = cb[w];
                     }
                     qsh[(size_t)pi * bd + tid] = (int16_t)q0;
                 }
@@ -150,25 +229,29 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
                         const int p1 = rot == 0 ? ab : (rot == 1 ? ab : ac);
                         const int p2i = rot == 0 ? ac : bc;
                         const long long qz = rot == 0 ? qbc : (rot == 1 ? qac : qab);
+                        // difference totals of the two pairs: A = (L^2 - q) / 2
+                        const int A1 = (L * L - (int)(p1 == ab ? qab : qac)) / 2;
+                        const int A2 = (L * L - (int)(p2i == ac ? qac : qbc)) / 2;
 #pragma unroll
                         for (int dir = 0; dir < 2; ++dir) {
-                            int n1[L], n2[L];
+                            uint32_t a1[NP], a2[NP], dd2[ND];
 #pragma unroll
-                            for (int c = 0; c < L; ++c) {
-                                n1[c] = nsh[(((size_t)p1 * 2 + dir) * L + c) * bd + tid];
-                                n2[c] = nsh[(((size_t)p2i * 2 + dir) * L + c) * bd + tid];
+                            for (int w = 0; w < NP; ++w) {
+                                a1[w] = nsh[(((size_t)p1 * 2 + dir) * NP + w) * bd + tid];
+                                a2[w] = nsh[(((size_t)p2i * 2 + dir) * NP + w) * bd + tid];
                             }
-#pragma unroll
-                            for (int d = 0; d <= H; ++d) {
-                                int s = 0;
-#pragma unroll
-                                for (int c = 0; c < L; ++c) {
-                                    const int m = (d == 0 || d == H) ? n2[(c + d) % L]
-                                                                     : n2[(c + d) % L] + n2[(c + L - d) % L];
-                                    s += n1[c] * m;
-                                }
-                                ft[d] += (int)qz * s;
-                            }
+                            cyclic_copy<L>(a2, dd2);
+                            // sum_c n1_c (n2_{c+d} + n2_{c-d}) with n = L - 2 a (one term at d = 0, L/2)
+                            for_d<0, H>([&](auto dc) {
+                                constexpr int d = decltype(dc)::value;
+                                int sv;
+                                if (d == 0 || d == H)
+                                    sv = L3 - 2 * L * (A1 + A2) + 4 * cyc_dot<L, d>(a1, dd2);
+                                else
+                                    sv = 2 * L3 - 4 * L * (A1 + A2) +
+                                         4 * (cyc_dot<L, d>(a1, dd2) + cyc_dot<L, (L - d) % L>(a1, dd2));
+                                ft[d] += (int)qz * sv;
+                            });
                         }
                     }
 #pragma unroll
@@ -215,7 +298,8 @@ size_t onetime_smem_bytes(const Group &g, int triples, int threads) {
     const int npair = g.R * (g.R - 1) / 2;
     const size_t pp = (size_t)npair * 8 + (size_t)2 * (g.L / 2 + 1) * threads * 8;
     if (!triples || g.R < 3 || g.R > kMaxTripleR) return pp;
-    return pp + (size_t)npair * (2 * g.L + 2) * threads;
+    const int np4 = 4 * ((g.L + 3) / 4);  // packed count bytes per vector
+    return pp + (size_t)npair * (2 * np4 + 2) * threads;
 }
 
 template <int L>
