@@ -322,9 +322,15 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *   QSG_OPT_ONETIME       0 = accumulate every one-time sum (default),
  *                         1 = skip the three-replica sums (chi3, F3 become
  *                         NaN); only before the first measurement
+ *   QSG_OPT_TAIL          0 = every slot in chunks of the same length
+ *                         (default); T > 0 = the wavefront launch of a group
+ *                         sweeps its last min(T, slots) slots in chunks of a
+ *                         quarter of the chunk length (when that is a multiple
+ *                         of 16), scheduled after all other units, so that
+ *                         short units fill the last wave of blocks
  * Results do not depend on the options: every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
-       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7 };
+       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7, QSG_OPT_TAIL = 8 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

@@ -178,6 +178,7 @@ struct qsg_ctx {
     int corr_tensor = 1;   // QSG_OPT_CORR_KERNEL: 1 tensor cores, 0 integer pipes
     int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 on
     int triples = 1;       // QSG_OPT_ONETIME: 1 with the three-replica sums, 0 without
+    int tail = 0;          // QSG_OPT_TAIL: slots swept in quarter-length chunks, last
     PlanBuffers pb;
     PersistentPlan plan{};
     bool plan_ok = false;
@@ -409,7 +410,7 @@ static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t
     for (const Group &g : ctx->groups) {
         const int C = ctx->sweep_kernel == 1 ? 0 : wavefront_chunk(g, ctx->chunk);
         if (C > 0)
-            QSG_CUDA(ctx, launch_sweep_wavefront(g, sb, idx, ctx->seed, g.arrivals, C, st));
+            QSG_CUDA(ctx, launch_sweep_wavefront(g, sb, idx, ctx->seed, g.arrivals, C, ctx->tail, st));
         else if (sb)
             return QSG_ERR_ARG;  // the reference kernel takes its index by value only
         else
@@ -420,8 +421,8 @@ static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t
 
 // (Re)capture the graph of graph_batch sweeps when a launch option changed.
 static qsg_status ensure_graph(qsg_ctx *ctx, bool persistent) {
-    const long long key = ((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 2 + (persistent ? 1 : 0)) * 2 +
-                           g_wavefront_variant) * 65537LL + ctx->chunk;
+    const long long key = (((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 2 + (persistent ? 1 : 0)) * 2 +
+                            g_wavefront_variant) * 65537LL + ctx->chunk) * 65537LL + ctx->tail;
     if (ctx->graph_exec && ctx->graph_key == key) return QSG_OK;
     if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
@@ -728,6 +729,11 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
     if (option == QSG_OPT_CORR_KERNEL) {
         if (value < 0 || value > 1) return QSG_ERR_ARG;
         ctx->corr_tensor = value == 0 ? 1 : 0;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_TAIL) {
+        if (value < 0 || value > (1 << 24)) return QSG_ERR_ARG;
+        ctx->tail = (int)value;
         return QSG_OK;
     }
     if (option == QSG_OPT_CHUNK) {

@@ -187,9 +187,11 @@ __device__ __forceinline__ void boundary_update(const Group &g, const Thr &t, ui
 // One work unit (slot s, chunk ch of C planes) run by the threads that share
 // `ring` (kRing * SLOT + 2 L^2 words of shared memory); threads with
 // active == false only take part in the barriers.  do_boundary is one int of
-// shared memory for this unit.
+// shared memory for this unit; the arrival counter of the boundary at the
+// start of chunk ch is arrivals[s * astride + ch].
 template <int ALGO, int SLOT, bool JREG = false>
-__device__ __forceinline__ void wavefront_unit(const Group &g, const int C, const int nch, const int s, const int ch,
+__device__ __forceinline__ void wavefront_unit(const Group &g, const int C, const int astride, const int s,
+                                               const int ch,
                                                const bool active, const int c, uint64_t *ring, int *do_boundary,
                                                const uint32_t sweep, const uint32_t k0, const uint32_t k1,
                                                unsigned *__restrict__ arrivals) {
@@ -354,12 +356,12 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
     // arrival at the two chunk boundaries: the second unit to arrive updates them
     __threadfence();
     __syncthreads();
-    const int chn = ch + 1 == nch ? 0 : ch + 1;
+    const int chn = b == Lt ? 0 : ch + 1;  // the chunk after the last is the first
     if (c == 0) {
         int flags = 0;
         if (active) {
-            if (atomicAdd(&arrivals[s * nch + ch], 1u) == 1u) flags |= 1;
-            if (atomicAdd(&arrivals[s * nch + chn], 1u) == 1u) flags |= 2;
+            if (atomicAdd(&arrivals[s * astride + ch], 1u) == 1u) flags |= 1;
+            if (atomicAdd(&arrivals[s * astride + chn], 1u) == 1u) flags |= 2;
             __threadfence();
         }
         *do_boundary = flags;
@@ -370,17 +372,21 @@ __device__ __forceinline__ void wavefront_unit(const Group &g, const int C, cons
         if (flags & 1) boundary_update<ALGO>(g, t, Sg, sJx, sJy, a, T, sweep, (uint32_t)s, k0, k1);
         if (flags & 2) boundary_update<ALGO>(g, t, Sg, sJx, sJy, b == Lt ? 0 : b, T, sweep, (uint32_t)s, k0, k1);
         if (c == 0) {
-            if (flags & 1) arrivals[s * nch + ch] = 0u;
-            if (flags & 2) arrivals[s * nch + chn] = 0u;
+            if (flags & 1) arrivals[s * astride + ch] = 0u;
+            if (flags & 2) arrivals[s * astride + chn] = 0u;
         }
     }
 }
 
-// One launch per sweep of one group: P units per block (blocks of P * L^2 / 2 threads).
+// One launch per sweep of one group: P units per block (blocks of P * L^2 / 2
+// threads).  Slots [0, S1) run nch chunks of C planes, slots [S1, nslots) nch2
+// chunks of C2 <= C planes; the units of the first slots come first, so that
+// the shorter units fill the last wave of blocks.
 template <int ALGO, int SLOT, int NREG, bool JREG = false>
 __global__ void __launch_bounds__(512) __maxnreg__(NREG)
-    k_sweep_wavefront(const Group g, const int C, const int nch, const int P, const uint32_t *sweep_base,
-                      const uint32_t sweep_off, const uint32_t k0, const uint32_t k1, unsigned *__restrict__ arrivals) {
+    k_sweep_wavefront(const Group g, const int C, const int nch, const int S1, const int C2, const int nch2,
+                      const int P, const uint32_t *sweep_base, const uint32_t sweep_off, const uint32_t k0,
+                      const uint32_t k1, unsigned *__restrict__ arrivals) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ int do_boundary[32];
     // absolute sweep index (keys Philox): a device counter plus an offset, so
@@ -389,11 +395,16 @@ __global__ void __launch_bounds__(512) __maxnreg__(NREG)
     const int L2 = g.L * g.L, tpu = L2 / 2;
     const int u = threadIdx.x / tpu, c = threadIdx.x - u * tpu;
     const int unit = blockIdx.x * P + u;
-    const bool active = unit < g.nslots * nch;
-    const int s = active ? unit / nch : 0;
-    const int ch = active ? unit - s * nch : 0;
-    wavefront_unit<ALGO, SLOT, JREG>(g, C, nch, s, ch, active, c, smem + (size_t)u * (kRing * SLOT + 2 * L2),
-                               &do_boundary[u], sweep, k0, k1, arrivals);
+    const int n1 = S1 * nch;
+    const bool active = unit < n1 + (g.nslots - S1) * nch2;
+    const bool first = unit < n1;
+    const int v = first ? unit : unit - n1;
+    const int nu = first ? nch : nch2;
+    const int s = active ? (first ? 0 : S1) + v / nu : 0;
+    const int ch = active ? v % nu : 0;
+    wavefront_unit<ALGO, SLOT, JREG>(g, first ? C : C2, nch2, s, ch, active, c,
+                                     smem + (size_t)u * (kRing * SLOT + 2 * L2), &do_boundary[u], sweep, k0, k1,
+                                     arrivals);
 }
 
 // One launch per sweep of several groups of different sizes (same algorithm):
@@ -458,12 +469,20 @@ int wavefront_units_per_block(const Group &g) {
     return P;
 }
 
+// Slots whose chunks are a quarter of C (the last `tail` slots), when C allows.
+static int tail_slots(const Group &g, int C, int tail) {
+    if (tail <= 0 || C < 64 || (C / 4) % 16 != 0) return 0;
+    return tail < g.nslots ? tail : g.nslots;
+}
+
 template <int ALGO, int SLOT, int NREG, bool JREG = false>
-static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
-                             unsigned *arrivals, cudaStream_t st) {
+static cudaError_t launch_wf(const Group &g, int C, int tail, const uint32_t *sweep_base, uint32_t sweep,
+                             uint64_t seed, unsigned *arrivals, cudaStream_t st) {
     const int nch = g.Ltau / C;
+    const int ts = tail_slots(g, C, tail);
+    const int C2 = ts > 0 ? C / 4 : C, nch2 = g.Ltau / C2, S1 = g.nslots - ts;
     const int P = wavefront_units_per_block(g);
-    const int units = g.nslots * nch;
+    const int units = S1 * nch + ts * nch2;
     const int blocks = (units + P - 1) / P;
     const size_t sm = (size_t)P * (kRing * SLOT + 2 * g.L * g.L) * sizeof(uint64_t);
     const int threads = P * (g.L * g.L / 2);
@@ -474,8 +493,8 @@ static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, 
                                  100);
     if (e != cudaSuccess) return e;
     count_launches(1);
-    k_sweep_wavefront<ALGO, SLOT, NREG, JREG><<<blocks, threads, sm, st>>>(g, C, nch, P, sweep_base, sweep, (uint32_t)seed,
-                                                                     (uint32_t)(seed >> 32), arrivals);
+    k_sweep_wavefront<ALGO, SLOT, NREG, JREG><<<blocks, threads, sm, st>>>(
+        g, C, nch, S1, C2, nch2, P, sweep_base, sweep, (uint32_t)seed, (uint32_t)(seed >> 32), arrivals);
     return cudaGetLastError();
 }
 
@@ -487,33 +506,33 @@ static cudaError_t launch_wf(const Group &g, int C, const uint32_t *sweep_base, 
 // couplings re-read from shared memory every step.  Blocks of more than 288
 // threads get 64.
 template <int ALGO, int SLOT>
-static cudaError_t launch_wf_slot(const Group &g, int C, const uint32_t *sb, uint32_t sweep, uint64_t seed,
+static cudaError_t launch_wf_slot(const Group &g, int C, int tail, const uint32_t *sb, uint32_t sweep, uint64_t seed,
                                   unsigned *arrivals, cudaStream_t st) {
     const int threads = wavefront_units_per_block(g) * (g.L * g.L / 2);
-    if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, sb, sweep, seed, arrivals, st);
-    if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, sb, sweep, seed, arrivals, st);
-    if (g_wavefront_variant == 2) return launch_wf<ALGO, SLOT, 96>(g, C, sb, sweep, seed, arrivals, st);
-    return launch_wf<ALGO, SLOT, 96, true>(g, C, sb, sweep, seed, arrivals, st);
+    if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (g_wavefront_variant == 2) return launch_wf<ALGO, SLOT, 96>(g, C, tail, sb, sweep, seed, arrivals, st);
+    return launch_wf<ALGO, SLOT, 96, true>(g, C, tail, sb, sweep, seed, arrivals, st);
 }
 
 // Ring planes are padded to the next of a few sizes (exact for L = 8, 12, 16,
 // 20, 24, 32).
 template <int ALGO>
-static cudaError_t launch_wf_algo(const Group &g, int C, const uint32_t *sb, uint32_t sweep, uint64_t seed,
+static cudaError_t launch_wf_algo(const Group &g, int C, int tail, const uint32_t *sb, uint32_t sweep, uint64_t seed,
                                   unsigned *arrivals, cudaStream_t st) {
     const int L2 = g.L * g.L;
-    if (L2 <= 64) return launch_wf_slot<ALGO, 64>(g, C, sb, sweep, seed, arrivals, st);
-    if (L2 <= 144) return launch_wf_slot<ALGO, 144>(g, C, sb, sweep, seed, arrivals, st);
-    if (L2 <= 256) return launch_wf_slot<ALGO, 256>(g, C, sb, sweep, seed, arrivals, st);
-    if (L2 <= 400) return launch_wf_slot<ALGO, 400>(g, C, sb, sweep, seed, arrivals, st);
-    if (L2 <= 576) return launch_wf_slot<ALGO, 576>(g, C, sb, sweep, seed, arrivals, st);
-    return launch_wf_slot<ALGO, 1024>(g, C, sb, sweep, seed, arrivals, st);
+    if (L2 <= 64) return launch_wf_slot<ALGO, 64>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (L2 <= 144) return launch_wf_slot<ALGO, 144>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (L2 <= 256) return launch_wf_slot<ALGO, 256>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (L2 <= 400) return launch_wf_slot<ALGO, 400>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (L2 <= 576) return launch_wf_slot<ALGO, 576>(g, C, tail, sb, sweep, seed, arrivals, st);
+    return launch_wf_slot<ALGO, 1024>(g, C, tail, sb, sweep, seed, arrivals, st);
 }
 
 cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
-                                   unsigned *arrivals, int C, cudaStream_t st) {
-    if (g.algo == 0) return launch_wf_algo<0>(g, C, sweep_base, sweep, seed, arrivals, st);
-    return launch_wf_algo<1>(g, C, sweep_base, sweep, seed, arrivals, st);
+                                   unsigned *arrivals, int C, int tail, cudaStream_t st) {
+    if (g.algo == 0) return launch_wf_algo<0>(g, C, tail, sweep_base, sweep, seed, arrivals, st);
+    return launch_wf_algo<1>(g, C, tail, sweep_base, sweep, seed, arrivals, st);
 }
 
 template <int ALGO>
@@ -674,7 +693,7 @@ extern "C" qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t
     g.Jy = const_cast<uint64_t *>(d_Jy);
     g.thr = (uint32_t *)thr;
     for (int it = 0; it < n_sweeps; ++it)
-        if (launch_sweep_wavefront(g, nullptr, first_sweep + (uint32_t)it, seed, (unsigned *)arr, C, st) != cudaSuccess)
+        if (launch_sweep_wavefront(g, nullptr, first_sweep + (uint32_t)it, seed, (unsigned *)arr, C, 0, st) != cudaSuccess)
             return QSG_ERR_CUDA;
     return QSG_OK;
 }

@@ -26,9 +26,10 @@ cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed
 int wavefront_chunk(const Group &g, int requested);
 extern int g_wavefront_variant;  // 0: register cap for 3 blocks/SM when blocks <= 288 threads; 1: 2 blocks/SM
 // The sweep index is *sweep_base + sweep (sweep_base may be null), so that a
-// captured CUDA graph of several sweeps can be replayed later.
+// captured CUDA graph of several sweeps can be replayed later.  The last
+// `tail` slots (0 = none) run chunks of C / 4 planes after every other unit.
 cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
-                                   unsigned *arrivals, int C, cudaStream_t st);
+                                   unsigned *arrivals, int C, int tail, cudaStream_t st);
 cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st);
 cudaError_t launch_add_word(uint32_t *p, uint32_t value, cudaStream_t st);
 

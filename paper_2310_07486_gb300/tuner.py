@@ -1,11 +1,13 @@
 """Launch-option autotuner for qsg_sweep.
 
 Every option of ``qsg_set_option`` that shapes the sweep launch (tau chunk per
-work unit, register variant, persistent multi-group launch, CUDA-graph batch)
-leaves the sampled bits unchanged, so the choice is purely one of speed.  The
-tuner times each valid combination on the caller's own context with CUDA
-events on the context's stream, keeps the fastest, and caches the choice in a
-JSON file keyed by the group shapes, the device name and the library build.
+work unit, register variant, persistent multi-group launch, CUDA-graph batch,
+slots swept in shorter chunks at the end of a launch) leaves the sampled bits
+unchanged, so the choice is purely one of speed.  The tuner times each valid
+combination of the first four on the caller's own context with CUDA events on
+the context's stream, then the tail length with the best of them, keeps the
+fastest, and caches the choice in a JSON file keyed by the group shapes, the
+device name and the library build.
 
 Tuning runs real sweeps, so the spins and counters of every group are saved
 to the host first and put back afterwards: a tuned run samples exactly what an
@@ -25,8 +27,9 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 
 # option id -> name used in the cache and in reports
 _NAMES = {Q.OPT_CHUNK: "chunk", Q.OPT_WAVEFRONT_VARIANT: "variant", Q.OPT_PERSISTENT: "persistent",
-          Q.OPT_GRAPH: "graph"}
-DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0}
+          Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail"}
+DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0}
+TAILS = [0, 16, 32, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
 
 
 def _library_id() -> str:
@@ -59,7 +62,7 @@ def candidates(shapes, sweeps_per_call):
     persistent = [1, 2] if len(shapes) > 1 else [1]
     graph = [0, sweeps_per_call] if sweeps_per_call > 1 else [0]
     for chunk, variant, pers, gr in itertools.product(chunks, [0, 1, 2], persistent, graph):
-        yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr}
+        yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0}
 
 
 def apply(ctx, choice: dict) -> None:
@@ -68,6 +71,7 @@ def apply(ctx, choice: dict) -> None:
     ctx.qsg_set_option(Q.OPT_CHUNK, int(choice["chunk"]))
     ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, int(choice["variant"]))
     ctx.qsg_set_option(Q.OPT_PERSISTENT, int(choice["persistent"]))
+    ctx.qsg_set_option(Q.OPT_TAIL, int(choice.get("tail", 0)))
     ctx.qsg_set_option(Q.OPT_GRAPH, int(choice["graph"]))
 
 
@@ -123,6 +127,19 @@ def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=Tr
             table.append((t, cand))
             if verbose:
                 print(f"  {cand} {t:.4f} ms/sweep", flush=True)
+        # second stage: the tail length with the best launch of the first
+        if table:
+            first = min(table, key=lambda tc: tc[0])[1]
+            for tail in TAILS[1:]:
+                cand = dict(first, tail=tail)
+                try:
+                    apply(ctx, cand)
+                except Q.QSGError:
+                    continue
+                t = _time_call(ctx, sweeps_per_call, reps)
+                table.append((t, cand))
+                if verbose:
+                    print(f"  {cand} {t:.4f} ms/sweep", flush=True)
     finally:
         for g, s in enumerate(spins):
             ctx.qsg_set_spins(g, s)
