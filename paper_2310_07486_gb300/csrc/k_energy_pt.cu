@@ -5,8 +5,10 @@
 namespace qsg {
 
 constexpr int kEnergyPlanes = 16;
-constexpr int kEnergyGroup = 10;  // planes per carry-save group: 3 * 10 <= 31 fits five bit planes
-constexpr int kEnergyRun = 120;   // tau planes per block (a multiple of the group)
+constexpr int kEnergyRun = 128;                // tau planes per block
+constexpr int kEnergyBuf = 8;                  // planes in the shared-memory ring
+constexpr int kEnergyAhead = kEnergyBuf - 2;   // planes in flight beyond the two being read
+constexpr int kEnergyFlush = 5;                // planes per carry-save group: 2 sites x 3 bonds x 5 <= 31
 
 // a += b for two bitsliced counters of kEnergyPlanes planes (ripple carry)
 __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const uint64_t (&b)[kEnergyPlanes]) {
@@ -19,62 +21,93 @@ __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const
     }
 }
 
+// (o16 o8 o4 o2 o1) += the unsatisfied-bond count of one site: its three
+// bond words go through a full adder into sum + 2 car
+__device__ __forceinline__ void count_site(uint64_t ux, uint64_t uy, uint64_t ut, uint64_t &o1, uint64_t &o2,
+                                           uint64_t &o4, uint64_t &o8, uint64_t &o16) {
+    const uint64_t sum = ux ^ uy ^ ut, car = (ux & uy) | (ut & (ux ^ uy));
+    const uint64_t h1 = o1 & sum;
+    o1 ^= sum;
+    const uint64_t h2 = (o2 & car) | (h1 & (o2 ^ car));
+    o2 ^= car ^ h1;
+    const uint64_t h4 = o4 & h2;
+    o4 ^= h2;
+    const uint64_t h8 = o8 & h4;
+    o8 ^= h4;
+    o16 ^= h8;
+}
+
 // U[slot][b] += number of unsatisfied bonds (J S S' = -1) among the three
 // forward bonds (+x, +y, +tau) of every site; each bond is counted once and
-// E = -(3N - 2U) is the action of Eq. (Trotter-action).  A block covers the
-// sites [xy0, xy0 + blockDim.x) of one slot over kEnergyRun planes, one thread
-// per site walking the planes with coalesced loads; the word of the next
-// plane, loaded as the +tau neighbour, is the next plane's own word.  The
-// three bond words of a site go through a full adder into a 5-bit carry-save
-// accumulator, added into the 10-plane per-thread counter once per
-// kEnergyGroup planes; the warp then sums its counters with shuffles and one
-// lane turns them into per-sample integers.
+// E = -(3N - 2U) is the action of Eq. (Trotter-action).  A block covers one
+// slot over kEnergyRun planes; its planes stream through a ring of
+// kEnergyBuf shared-memory planes filled by cp.async kEnergyAhead planes
+// ahead, so every word is read from HBM once and the +x, +y and +tau
+// neighbours come from shared memory.  A thread owns two adjacent site words
+// of a row; their bond counts go through a 5-bit carry-save accumulator,
+// added into the kEnergyPlanes-plane per-thread counter every kEnergyFlush
+// planes; the warp then sums its counters with shuffles and one lane turns
+// them into per-sample integers.
 __global__ void __launch_bounds__(512) k_energy(Group g) {
+    extern __shared__ __align__(16) uint64_t eplanes[];  // [kEnergyBuf][L^2]
     __shared__ int cnt[64];
-    const int s = blockIdx.y;
+    const int s = blockIdx.x;
     const int L = g.L, L2 = L * L, Lt = g.Ltau;
     const int w = s / (g.R * g.K);
     const uint64_t *S = g.S + (size_t)s * g.N;
     for (int b = threadIdx.x; b < 64; b += blockDim.x) cnt[b] = 0;
-    __syncthreads();
+    const int t0 = blockIdx.y * kEnergyRun, t1 = min(t0 + kEnergyRun, Lt);
+    const int xy = 2 * (int)threadIdx.x;
+    const bool own = xy < L2;  // sites xy and xy + 1 (L is even: one row)
+    // plane q of the block (t0 <= q <= t1; q = Lt is plane 0) into ring slot q % kEnergyBuf
+    auto issue = [&](int q) {
+        if (own && q <= t1) {
+            const int gq = q == Lt ? 0 : q;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(eplanes + (size_t)(q % kEnergyBuf) * L2 + xy);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(S + (size_t)gq * L2 + xy)
+                         : "memory");
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
     uint64_t c[kEnergyPlanes];
 #pragma unroll
     for (int p = 0; p < kEnergyPlanes; ++p) c[p] = 0;
-    const int xy = blockIdx.x * blockDim.x + threadIdx.x;
-    const int t0 = blockIdx.z * kEnergyRun, t1 = min(t0 + kEnergyRun, Lt);
-    if (xy < L2) {
-        const int y = xy / L, x = xy - y * L;
-        const int xr = y * L + (x + 1 == L ? 0 : x + 1), yu = (y + 1 == L ? 0 : y + 1) * L + x;
-        const uint64_t jx = g.Jx[(size_t)w * L2 + xy], jy = g.Jy[(size_t)w * L2 + xy];
-        const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
-        uint64_t v = __ldg(S + (size_t)t0 * L2 + xy);
-        for (int tb = t0; tb < t1; tb += kEnergyGroup) {
-            uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0, o16 = 0;
+    int xr = 0, yu = 0;
+    uint64_t j0x = 0, j1x = 0, j0y = 0, j1y = 0;
+    if (own) {
+        const int y = xy / L, x = xy - y * L;  // x even, x + 1 < L
+        xr = y * L + (x + 2 == L ? 0 : x + 2);  // right neighbour of site xy + 1
+        yu = (y + 1 == L ? 0 : y + 1) * L + x;  // up neighbours: yu, yu + 1
+        j0x = g.Jx[(size_t)w * L2 + xy];
+        j1x = g.Jx[(size_t)w * L2 + xy + 1];
+        j0y = g.Jy[(size_t)w * L2 + xy];
+        j1y = g.Jy[(size_t)w * L2 + xy + 1];
+    }
+    const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
 #pragma unroll
-            for (int k = 0; k < kEnergyGroup; ++k) {
-                const int t = tb + k;
-                if (t < t1) {
-                    const uint64_t *P = S + (size_t)t * L2;
-                    const bool wrap = t + 1 == Lt;
-                    const uint64_t vt = __ldg(S + (size_t)(wrap ? 0 : t + 1) * L2 + xy);
-                    const uint64_t ux = v ^ __ldg(P + xr) ^ jx, uy = v ^ __ldg(P + yu) ^ jy;
-                    const uint64_t ut = v ^ vt ^ (wrap ? apbc : 0ull);
-                    const uint64_t sum = ux ^ uy ^ ut, car = (ux & uy) | (ut & (ux ^ uy));
-                    // (o16 o8 o4 o2 o1) += sum + 2 car
-                    const uint64_t h1 = o1 & sum;
-                    o1 ^= sum;
-                    const uint64_t h2 = (o2 & car) | (h1 & (o2 ^ car));
-                    o2 ^= car ^ h1;
-                    const uint64_t h4 = o4 & h2;
-                    o4 ^= h2;
-                    const uint64_t h8 = o8 & h4;
-                    o8 ^= h4;
-                    o16 ^= h8;  // at most 3 * 10 = 30 per position: no carry out of o16
-                    v = vt;
-                }
-            }
+    for (int d = 0; d <= kEnergyAhead; ++d) issue(t0 + d);
+    uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0, o16 = 0;
+    int ng = 0;
+    for (int q = t0; q < t1; ++q) {
+        // planes q and q + 1 have landed (q + 2 .. q + kEnergyAhead may be in flight)
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEnergyAhead - 1) : "memory");
+        __syncthreads();
+        // the slot of plane q - 1 is free for every thread: refill it
+        issue(q + kEnergyAhead + 1);
+        if (own) {
+            const uint64_t *P = eplanes + (size_t)(q % kEnergyBuf) * L2;
+            const uint64_t *Pn = eplanes + (size_t)((q + 1) % kEnergyBuf) * L2;
+            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(P + xy);
+            const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(P + yu);
+            const ulonglong2 n = *reinterpret_cast<const ulonglong2 *>(Pn + xy);
+            const uint64_t r1 = P[xr];
+            const uint64_t ft = q + 1 == Lt ? apbc : 0ull;
+            count_site(v.x ^ v.y ^ j0x, v.x ^ u.x ^ j0y, v.x ^ n.x ^ ft, o1, o2, o4, o8, o16);
+            count_site(v.y ^ r1 ^ j1x, v.y ^ u.y ^ j1y, v.y ^ n.y ^ ft, o1, o2, o4, o8, o16);
+        }
+        if (++ng == kEnergyFlush || q + 1 == t1) {
             // c += (o16 o8 o4 o2 o1): ripple over the low planes (a thread counts
-            // at most 3 * kEnergyRun < 2^9 per position)
+            // at most 6 * kEnergyRun < 2^10 per position)
             uint64_t carry = 0;
             const uint64_t in[5] = {o1, o2, o4, o8, o16};
 #pragma unroll
@@ -84,9 +117,12 @@ __global__ void __launch_bounds__(512) k_energy(Group g) {
                 carry = (c[p] & b) | (carry & (c[p] ^ b));
                 c[p] = sp;
             }
+            o1 = o2 = o4 = o8 = o16 = 0;
+            ng = 0;
         }
     }
-    // warp sum of the bitsliced counters (at most 32 * 3 * kEnergyRun < 2^14)
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // warp sum of the bitsliced counters (at most 32 * 6 * kEnergyRun < 2^15)
     for (int o = 16; o > 0; o >>= 1) {
         uint64_t other[kEnergyPlanes];
 #pragma unroll
@@ -114,13 +150,17 @@ __global__ void __launch_bounds__(512) k_energy(Group g) {
 cudaError_t launch_energy(const Group &g, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(g.U, 0, sizeof(int32_t) * (size_t)g.nslots * 64, st);
     if (e != cudaSuccess) return e;
-    // blocks of at most 512 threads tiling the plane with the fewest idle threads
+    // one thread per two site words; a ring of kEnergyBuf planes in shared memory
     const int L2 = g.L * g.L;
-    const int nblk = (L2 + 511) / 512;
-    const int threads = ((L2 + nblk - 1) / nblk + 31) / 32 * 32;
-    dim3 grid(nblk, g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
+    const int threads = (L2 / 2 + 31) / 32 * 32;
+    const size_t sm = (size_t)kEnergyBuf * L2 * sizeof(uint64_t);
+    if (sm > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
     count_launches(1);
-    k_energy<<<grid, threads, 0, st>>>(g);
+    k_energy<<<grid, threads, sm, st>>>(g);
     return cudaGetLastError();
 }
 
