@@ -29,7 +29,7 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 _NAMES = {Q.OPT_CHUNK: "chunk", Q.OPT_WAVEFRONT_VARIANT: "variant", Q.OPT_PERSISTENT: "persistent",
           Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail"}
 DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0}
-TAILS = [0, 16, 32, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
+TAILS = [0, 16, 24, 32, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
 
 
 def _library_id() -> str:
@@ -45,7 +45,7 @@ def cache_key(shapes, device_name: str) -> str:
     return hashlib.sha256(f"{desc}|{device_name}|{_library_id()}".encode()).hexdigest()[:24]
 
 
-def candidate_chunks(shapes, largest=256):
+def candidate_chunks(shapes, largest=512):
     """Tau planes per work unit that every group accepts: multiples of 16
     dividing every L_tau, plus 0 (the library's own choice)."""
     out = [0]

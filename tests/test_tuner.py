@@ -14,7 +14,7 @@ from paper_2310_07486_gb300 import tuner
 def test_candidate_chunks_divide_every_ltau():
     shapes = [Q.Shape(8, 96, 64, 1, 2), Q.Shape(12, 64, 64, 1, 2)]
     assert tuner.candidate_chunks(shapes) == [0, 16, 32]
-    assert tuner.candidate_chunks([Q.Shape(24, 2048, 64, 1, 1)]) == [0, 16, 32, 64, 128, 256]
+    assert tuner.candidate_chunks([Q.Shape(24, 2048, 64, 1, 1)]) == [0, 16, 32, 64, 128, 256, 512]
     assert tuner.candidate_chunks([Q.Shape(8, 24, 64, 1, 1)]) == [0]
 
 
