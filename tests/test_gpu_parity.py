@@ -479,12 +479,12 @@ def test_correlator_readback_into_caller_buffers(pinned):
         assert np.array_equal(got[k], ref[k])
 
 
-@pytest.mark.parametrize("chunk,tail", [(64, 3), (128, 12), (64, 100)])
-def test_wavefront_tail_slots_in_short_chunks_match_oracle(chunk, tail):
+@pytest.mark.parametrize("Ltau,chunk,tail", [(128, 64, 3), (128, 128, 12), (128, 64, 100), (1024, 512, 5)])
+def test_wavefront_tail_slots_in_short_chunks_match_oracle(Ltau, chunk, tail):
     """The last `tail` slots swept in quarter-length chunks after every other
     unit (arrival counters at the finer spacing) give the oracle's bits; a
     tail longer than the group covers every slot."""
-    shape = Q.Shape(8, 128, 70, 2, 3, Q.HEATBATH, Q.APBC)
+    shape = Q.Shape(8, Ltau, 70, 2, 3, Q.HEATBATH, Q.APBC)
     ctx, orc = _pair(shape, np.array([0.25, 0.3, 0.35]), seed=19)
     ctx.qsg_set_option(Q.OPT_CHUNK, chunk)
     ctx.qsg_set_option(Q.OPT_TAIL, tail)
