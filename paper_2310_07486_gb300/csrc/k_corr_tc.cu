@@ -355,18 +355,35 @@ __global__ void __launch_bounds__(kThreads, 1)
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&ctl.accempty[a]);
                         const int o0 = obase + cbase - m;  // offset of column q is o0 + q
-                        if (full && cls != 2 && jb != i) {
-                            // every element of the tile folds the same way:
-                            // lag o0 + q (all o < L_tau/2) or L_tau - o0 - q
-                            const int base = cls == 0 ? o0 : Lt - o0, step = cls == 0 ? 1 : -1;
-                            const int sgn = cls == 0 ? 1 : whigh;
-                            int *bc = binC + base;
-                            unsigned *bq = binQ + base;
+                        if (full && cls == 0 && jb != i) {
+                            // every element folds to lag o0 + q (all o < L_tau/2)
+                            int *bc = binC + o0;
+                            unsigned *bq = binQ + o0;
 #pragma unroll
                             for (int q = 0; q < 64; ++q) {
                                 const int gv = exact_f32_to_int(v[q]);
-                                atomicAdd(bc + step * q, sgn * gv);
-                                atomicAdd(bq + step * q, (unsigned)(gv * gv));
+                                atomicAdd(bc + q, gv);
+                                atomicAdd(bq + q, (unsigned)(gv * gv));
+                            }
+                        } else if (full && cls == 1) {
+                            // every element folds to lag L_tau - o0 - q, the wrapped
+                            // forward pair (APBC: C takes the minus sign)
+                            int *bc = binC + (Lt - o0);
+                            unsigned *bq = binQ + (Lt - o0);
+                            if (whigh == 1) {
+#pragma unroll
+                                for (int q = 0; q < 64; ++q) {
+                                    const int gv = exact_f32_to_int(v[q]);
+                                    atomicAdd(bc - q, gv);
+                                    atomicAdd(bq - q, (unsigned)(gv * gv));
+                                }
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < 64; ++q) {
+                                    const int gv = exact_f32_to_int(v[q]);
+                                    atomicAdd(bc - q, -gv);
+                                    atomicAdd(bq - q, (unsigned)(gv * gv));
+                                }
                             }
                         } else if (t1 < Lt) {
 #pragma unroll
