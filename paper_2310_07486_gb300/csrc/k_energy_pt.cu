@@ -5,10 +5,10 @@
 namespace qsg {
 
 constexpr int kEnergyPlanes = 16;
-constexpr int kEnergyRun = 128;                // tau planes per block
+constexpr int kEnergyRun = 128;                // tau planes per block (even)
 constexpr int kEnergyBuf = 8;                  // planes in the shared-memory ring
-constexpr int kEnergyAhead = kEnergyBuf - 2;   // planes in flight beyond the two being read
-constexpr int kEnergyFlush = 5;                // planes per carry-save group: 2 sites x 3 bonds x 5 <= 31
+constexpr int kEnergyAhead = kEnergyBuf - 3;   // planes in flight beyond the three being read
+constexpr int kEnergyFlush = 4;                // planes per carry-save group: 2 sites x 3 bonds x 4 <= 31
 
 // a += b for two bitsliced counters of kEnergyPlanes planes (ripple carry)
 __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const uint64_t (&b)[kEnergyPlanes]) {
@@ -40,15 +40,15 @@ __device__ __forceinline__ void count_site(uint64_t ux, uint64_t uy, uint64_t ut
 // U[slot][b] += number of unsatisfied bonds (J S S' = -1) among the three
 // forward bonds (+x, +y, +tau) of every site; each bond is counted once and
 // E = -(3N - 2U) is the action of Eq. (Trotter-action).  A block covers one
-// slot over kEnergyRun planes; its planes stream through a ring of
-// kEnergyBuf shared-memory planes filled by cp.async kEnergyAhead planes
-// ahead, so every word is read from HBM once and the +x, +y and +tau
-// neighbours come from shared memory.  A thread owns two adjacent site words
+// slot over kEnergyRun planes, two planes per block barrier; its planes
+// stream through a ring of kEnergyBuf shared-memory planes filled by cp.async
+// kEnergyAhead planes ahead, so every word is read from HBM once and the +x,
+// +y and +tau neighbours come from shared memory.  A thread owns two adjacent site words
 // of a row; their bond counts go through a 5-bit carry-save accumulator,
 // added into the kEnergyPlanes-plane per-thread counter every kEnergyFlush
 // planes; the warp then sums its counters with shuffles and one lane turns
 // them into per-sample integers.
-__global__ void __launch_bounds__(512) k_energy(Group g) {
+__global__ void __launch_bounds__(512, 2) k_energy(Group g) {
     extern __shared__ __align__(16) uint64_t eplanes[];  // [kEnergyBuf][L^2]
     __shared__ int cnt[64];
     const int s = blockIdx.x;
@@ -88,24 +88,30 @@ __global__ void __launch_bounds__(512) k_energy(Group g) {
     for (int d = 0; d <= kEnergyAhead; ++d) issue(t0 + d);
     uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0, o16 = 0;
     int ng = 0;
-    for (int q = t0; q < t1; ++q) {
-        // planes q and q + 1 have landed (q + 2 .. q + kEnergyAhead may be in flight)
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEnergyAhead - 1) : "memory");
+    auto plane = [&](int q) {
+        const uint64_t *P = eplanes + (size_t)(q % kEnergyBuf) * L2;
+        const uint64_t *Pn = eplanes + (size_t)((q + 1) % kEnergyBuf) * L2;
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(P + xy);
+        const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(P + yu);
+        const ulonglong2 n = *reinterpret_cast<const ulonglong2 *>(Pn + xy);
+        const uint64_t r1 = P[xr];
+        const uint64_t ft = q + 1 == Lt ? apbc : 0ull;
+        count_site(v.x ^ v.y ^ j0x, v.x ^ u.x ^ j0y, v.x ^ n.x ^ ft, o1, o2, o4, o8, o16);
+        count_site(v.y ^ r1 ^ j1x, v.y ^ u.y ^ j1y, v.y ^ n.y ^ ft, o1, o2, o4, o8, o16);
+    };
+    for (int q = t0; q < t1; q += 2) {
+        // planes q, q + 1 and q + 2 have landed (q + 3 .. q + kEnergyAhead may be in flight)
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEnergyAhead - 2) : "memory");
         __syncthreads();
-        // the slot of plane q - 1 is free for every thread: refill it
+        // the slots of planes q - 2 and q - 1 are free for every thread: refill them
         issue(q + kEnergyAhead + 1);
+        issue(q + kEnergyAhead + 2);
         if (own) {
-            const uint64_t *P = eplanes + (size_t)(q % kEnergyBuf) * L2;
-            const uint64_t *Pn = eplanes + (size_t)((q + 1) % kEnergyBuf) * L2;
-            const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(P + xy);
-            const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(P + yu);
-            const ulonglong2 n = *reinterpret_cast<const ulonglong2 *>(Pn + xy);
-            const uint64_t r1 = P[xr];
-            const uint64_t ft = q + 1 == Lt ? apbc : 0ull;
-            count_site(v.x ^ v.y ^ j0x, v.x ^ u.x ^ j0y, v.x ^ n.x ^ ft, o1, o2, o4, o8, o16);
-            count_site(v.y ^ r1 ^ j1x, v.y ^ u.y ^ j1y, v.y ^ n.y ^ ft, o1, o2, o4, o8, o16);
+            plane(q);
+            if (q + 1 < t1) plane(q + 1);
         }
-        if (++ng == kEnergyFlush || q + 1 == t1) {
+        ng += 2;
+        if (ng == kEnergyFlush || q + 2 >= t1) {
             // c += (o16 o8 o4 o2 o1): ripple over the low planes (a thread counts
             // at most 6 * kEnergyRun < 2^10 per position)
             uint64_t carry = 0;
