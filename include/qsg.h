@@ -350,11 +350,17 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
  * The kernel's scratch (its chunk-boundary arrival counters and the
  * acceptance table) lives in two fixed arrays in device memory that every GPU
  * loading this library holds until the process exits: at most 2^20 counters
- * (slots x tau chunks) and 128 ladder positions; larger shapes are rejected
- * with QSG_ERR_ARG, shapes with L_tau not a multiple of 16 with QSG_ERR_SHAPE.
- * The first call on a device looks the arrays up and clears the counters, so
- * it should come before any stream capture on that device.  Every call shares
- * the same arrays: calls that overlap on the GPU (other streams, other host
+ * (slots x tau chunks) and 128 ladder positions.  Shapes beyond these limits
+ * are rejected with QSG_ERR_WORKSPACE before any pointer is looked at; shapes
+ * with L_tau not a multiple of 16 (or otherwise invalid) with QSG_ERR_SHAPE;
+ * null buffers, a bad ladder or a cuda_stream that does not belong to the
+ * current device with QSG_ERR_ARG.  The library cannot check the sizes of the
+ * caller's buffers: they must hold the words given above.
+ * The first call on a device (with that device current) looks the arrays up
+ * and clears the counters, so it should come before any stream capture on
+ * that device; the addresses are cached per device and do not survive
+ * cudaDeviceReset.  Every call shares the same arrays, which keep the last
+ * call's contents: calls that overlap on the GPU (other streams, other host
  * threads) race and must be serialised by the caller.  The call copies the
  * table to the device and waits for that copy on cuda_stream; the sweeps are
  * enqueued on cuda_stream without waiting.  Nothing is allocated. */

@@ -153,6 +153,26 @@ uint32_t hb_threshold(double k, int h) {
     return (uint32_t)t;
 }
 
+}  // namespace
+
+bool qsg::build_accept_tables(const double *k, int K, uint32_t *table) {
+    for (int j = 0; j < K; ++j) {
+        if (!(k[j] > 0.0) || !(k[j] < 3.0)) return false;
+        if (j > 0 && !(k[j] > k[j - 1])) return false;
+        uint32_t *t = table + 16 * (size_t)j;
+        for (int n = 0; n < 16; ++n) t[n] = 0u;
+        for (int c = 0; c < 3; ++c) t[c] = met_threshold(k[j], 2 * (c + 1));
+        for (int n = 0; n < 7; ++n) t[8 + n] = hb_threshold(k[j], 6 - 2 * n);
+        for (int c = 0; c < 2; ++c)
+            if (t[c] < t[c + 1]) return false;
+        for (int n = 0; n < 6; ++n)
+            if (t[8 + n] < t[9 + n]) return false;
+    }
+    return true;
+}
+
+namespace {
+
 uint64_t pt_factor(double delta, long long n) {
     return (uint64_t)std::floor(std::exp(-(delta * (double)n)) * 4294967296.0);
 }
@@ -310,22 +330,10 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
     const double *lad = k_ladders;
     for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
         const Group &g = ctx->groups[gi];
-        for (int j = 0; j < g.K; ++j) {
-            if (!(lad[j] > 0.0) || !(lad[j] < 3.0)) return QSG_ERR_ARG;
-            if (j > 0 && !(lad[j] > lad[j - 1])) return QSG_ERR_ARG;
-        }
+        thr[gi].assign(16 * (size_t)g.K, 0u);
+        if (!build_accept_tables(lad, g.K, thr[gi].data())) return QSG_ERR_ARG;
         // cos(2 pi d / L) of the momentum sums of the one-time observables
         for (int d = 0; d <= g.L / 2; ++d) wcos[gi].push_back(std::cos(2.0 * 3.14159265358979323846 * d / g.L));
-        thr[gi].assign(16 * (size_t)g.K, 0u);
-        for (int j = 0; j < g.K; ++j) {
-            for (int c = 0; c < 3; ++c) thr[gi][16 * j + c] = met_threshold(lad[j], 2 * (c + 1));
-            for (int n = 0; n < 7; ++n) thr[gi][16 * j + 8 + n] = hb_threshold(lad[j], 6 - 2 * n);
-            // the bitsliced comparison in the sweep kernels relies on monotone tables
-            for (int c = 0; c < 2; ++c)
-                if (thr[gi][16 * j + c] < thr[gi][16 * j + c + 1]) return QSG_ERR_ARG;
-            for (int n = 0; n < 6; ++n)
-                if (thr[gi][16 * j + 8 + n] < thr[gi][16 * j + 9 + n]) return QSG_ERR_ARG;
-        }
         const int np = g.K > 1 ? g.K - 1 : 1;
         const long long nmax_blocks = (6LL * g.N >> 6) + 1;
         B[gi].assign(64 * (size_t)np, 0);

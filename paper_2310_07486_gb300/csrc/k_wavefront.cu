@@ -604,17 +604,15 @@ std::mutex g_static_mutex;
 void *g_static_arrivals_ptr[kMaxDevices];
 void *g_static_thr_ptr[kMaxDevices];
 
-// Device addresses of the two arrays on the current device (looked up and the
-// counters cleared on the first call on that device).
-cudaError_t static_scratch(void **arrivals, void **thr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
+// Device addresses of the two arrays on device `dev`, which must be current
+// (looked up, and the counters cleared, on the first call on that device).
+// The addresses are cached per device; they do not survive cudaDeviceReset.
+cudaError_t static_scratch(int dev, void **arrivals, void **thr) {
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_mutex);
     if (!g_static_arrivals_ptr[dev]) {
         void *a = nullptr, *t = nullptr;
-        e = cudaGetSymbolAddress(&a, g_static_arrivals);
+        cudaError_t e = cudaGetSymbolAddress(&a, g_static_arrivals);
         if (e != cudaSuccess) return e;
         e = cudaGetSymbolAddress(&t, g_static_thr);
         if (e != cudaSuccess) return e;
@@ -636,14 +634,15 @@ extern "C" qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t
                                                uint64_t seed, uint32_t first_sweep, int32_t n_sweeps,
                                                void *cuda_stream) {
     using namespace qsg;
-    if (!d_spins || !d_Jx || !d_Jy || !shape || !k_ladder || n_sweeps < 0 || group_id < 0 || group_id > 255)
-        return QSG_ERR_ARG;
+    // shape and limits first, so that an oversized shape is reported as such
+    // whatever the buffers are
+    if (!shape) return QSG_ERR_ARG;
     const qsg_shape &sh = *shape;
     if (sh.L < 2 || sh.L > 32 || (sh.L & 1) || sh.Ltau < 16 || sh.Ltau > 65536 || sh.n_samples < 1 ||
-        sh.n_replicas < 1 || sh.n_k < 1 || (sh.algo != QSG_METROPOLIS && sh.algo != QSG_HEATBATH) ||
+        sh.n_replicas < 1 || sh.n_replicas > 1023 || sh.n_k < 1 ||
+        (sh.algo != QSG_METROPOLIS && sh.algo != QSG_HEATBATH) ||
         (sh.boundary != QSG_PBC && sh.boundary != QSG_APBC) || sh.reserved != 0)
         return QSG_ERR_SHAPE;
-    if ((uint64_t)first_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
     Group g;
     memset(&g, 0, sizeof(g));
     g.L = sh.L;
@@ -659,28 +658,25 @@ extern "C" qsg_status qsg_sweep_static_scratch(uint64_t *d_spins, const uint64_t
     g.nlag = sh.Ltau / 2 + 1;
     g.n_samples = sh.n_samples;
     g.nwx = (sh.L * sh.L + 63) / 64;
+    if ((long long)g.W * g.R * g.K > (1LL << 30)) return QSG_ERR_SHAPE;
     const int C = wavefront_chunk(g, 0);
     if (C == 0) return QSG_ERR_SHAPE;  // L_tau must be a multiple of 16
     // the limits of the static scratch
-    if (g.K > kStaticMaxK || (long long)g.nslots * (g.Ltau / C) > kStaticArrivals) return QSG_ERR_ARG;
-    // acceptance table (same definitions as qsg_init_samples), on the stack
+    if (g.K > kStaticMaxK || (long long)g.nslots * (g.Ltau / C) > kStaticArrivals) return QSG_ERR_WORKSPACE;
+    if (!d_spins || !d_Jx || !d_Jy || !k_ladder || n_sweeps < 0 || group_id < 0 || group_id > 255)
+        return QSG_ERR_ARG;
+    if ((uint64_t)first_sweep + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
+    // acceptance table (the definitions of qsg_init_samples), on the stack
     uint32_t table[kStaticMaxK * 16];
-    for (int j = 0; j < g.K; ++j) {
-        const double k = k_ladder[j];
-        if (!(k > 0.0) || !(k < 3.0) || (j > 0 && !(k > k_ladder[j - 1]))) return QSG_ERR_ARG;
-        for (int n = 0; n < 16; ++n) table[16 * j + n] = 0u;
-        for (int c = 0; c < 3; ++c)
-            table[16 * j + c] = (uint32_t)std::floor(std::exp(-(2.0 * k * (double)(2 * (c + 1)))) * 4294967296.0);
-        for (int n = 0; n < 7; ++n) {
-            const double p = 1.0 / (1.0 + std::exp(-(2.0 * k * (double)(6 - 2 * n))));
-            double t = std::floor(p * 4294967296.0);
-            if (t > 4294967295.0) t = 4294967295.0;
-            table[16 * j + 8 + n] = (uint32_t)t;
-        }
-    }
-    void *arr = nullptr, *thr = nullptr;
-    if (static_scratch(&arr, &thr) != cudaSuccess) return QSG_ERR_CUDA;
+    if (!build_accept_tables(k_ladder, g.K, table)) return QSG_ERR_ARG;
+    // the scratch is looked up on the current device: the stream must belong to it
     cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, sdev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QSG_ERR_CUDA;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) return QSG_ERR_ARG;
+    if (sdev != dev) return QSG_ERR_ARG;
+    void *arr = nullptr, *thr = nullptr;
+    if (static_scratch(dev, &arr, &thr) != cudaSuccess) return QSG_ERR_CUDA;
     // the table lives on this function's stack: copy it and wait for the copy
     if (cudaMemcpyAsync(thr, table, sizeof(uint32_t) * 16 * (size_t)g.K, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return QSG_ERR_CUDA;

@@ -11,6 +11,13 @@ namespace qsg {
 // Process-wide count of kernel launches (qsg_kernel_launches()).
 void count_launches(int n);
 
+// Acceptance tables of a ladder k[0..K) (host FP64, integer results), 16 words
+// per ladder position: [0..2] Metropolis thresholds for S h = 2, 4, 6, [8..14]
+// heat-bath thresholds for h = 6 - 2 n, the rest zero.  False if the ladder is
+// not 0 < k_0 < ... < k_{K-1} < 3 or a table is not monotone (the bitsliced
+// comparison of the sweep kernels relies on monotone tables).
+bool build_accept_tables(const double *k, int K, uint32_t *table);
+
 // Device-side status word: non-zero after a bounded wait gave up.
 enum : int { DEVERR_NONE = 0, DEVERR_TIMEOUT = 1 };
 

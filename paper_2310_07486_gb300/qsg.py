@@ -138,11 +138,27 @@ def exported_symbols():
 def qsg_sweep_static_scratch(spins, Jx, Jy, shape: "Shape", group_id, ladder, seed, first_sweep, n_sweeps,
                              stream=None):
     """Sweeps on caller-owned device buffers (torch tensors of 64-bit words)
-    without any device allocation by the library."""
+    without any device allocation by the library.
+
+    The C entry point cannot see the sizes of the buffers, so they are checked
+    here: int64, contiguous, on the stream's device, spins of
+    slots * L_tau * L * L words and couplings of words * L * L words each."""
     import torch
-    lad = np.ascontiguousarray(np.asarray(ladder, dtype=np.float64))
+    lad = np.ascontiguousarray(np.asarray(ladder, dtype=np.float64).ravel())
     sh = shape.c()
     st = stream if stream is not None else torch.cuda.current_stream()
+    want = {"spins": shape.slots * shape.Ltau * shape.L * shape.L, "Jx": shape.words * shape.L * shape.L,
+            "Jy": shape.words * shape.L * shape.L}
+    for name, t in (("spins", spins), ("Jx", Jx), ("Jy", Jy)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()):
+            raise QSGError(-1, "qsg_sweep_static_scratch", "%s must be a contiguous int64 CUDA tensor" % name)
+        if t.device != st.device:
+            raise QSGError(-1, "qsg_sweep_static_scratch", "%s is not on the stream's device" % name)
+        if t.numel() != want[name]:
+            raise QSGError(-1, "qsg_sweep_static_scratch", "%s holds %d words, the shape needs %d"
+                           % (name, t.numel(), want[name]))
+    if lad.size != shape.n_k:
+        raise QSGError(-1, "qsg_sweep_static_scratch", "ladder has %d values, n_k is %d" % (lad.size, shape.n_k))
     status = load_library().qsg_sweep_static_scratch(
         ctypes.c_void_p(spins.data_ptr()), ctypes.c_void_p(Jx.data_ptr()), ctypes.c_void_p(Jy.data_ptr()),
         ctypes.byref(sh), int(group_id), _ptr(lad), int(seed) & ((1 << 64) - 1), int(first_sweep), int(n_sweeps),

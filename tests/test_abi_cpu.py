@@ -6,6 +6,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 from paper_2310_07486_gb300 import qsg as Q
@@ -64,3 +65,37 @@ def test_calls_on_null_context_fail_cleanly():
     assert lib.qsg_tempering_swap(None) == -1
     assert lib.qsg_measure_correlators(None) == -1
     assert lib.qsg_strerror(-4) == b"bounded device wait gave up"
+
+
+def test_static_scratch_checks_shape_and_limits_before_buffers():
+    """The allocation-free sweep rejects shapes beyond its fixed scratch with
+    QSG_ERR_WORKSPACE before it looks at the buffers; with null buffers a
+    regressed limit check would answer QSG_ERR_ARG instead, and never launch."""
+    lib = Q.load_library()
+
+    def call(shape, ladder):
+        sh = shape.c()
+        lad = np.ascontiguousarray(ladder, dtype=np.float64)
+        return lib.qsg_sweep_static_scratch(None, None, None, ctypes.byref(sh), 0, Q._ptr(lad), 1, 0, 1, None)
+
+    lad = np.linspace(0.1, 0.5, 129)
+    assert call(Q.Shape(8, 24, 64, 1, 1), [0.3]) == -2  # L_tau not a multiple of 16
+    assert call(Q.Shape(7, 16, 64, 1, 1), [0.3]) == -2  # odd L
+    assert call(Q.Shape(8, 16, 64, 1, 129), lad) == -6  # more ladder positions than the static table
+    assert call(Q.Shape(8, 16, 64 * 512, 64, 128), lad[:128]) == -6  # more slots x chunks than the counters
+    assert call(Q.Shape(8, 16, 64, 1, 1), [0.3]) == -1  # null buffers
+    sh = Q.Shape(8, 16, 64, 1, 1).c()
+    assert lib.qsg_sweep_static_scratch(None, None, None, None, 0, None, 1, 0, 1, None) == -1  # null shape
+
+
+def test_static_scratch_wrapper_requires_device_tensors():
+    torch = pytest.importorskip("torch")
+
+    class _Stream:  # stands in for a CUDA stream; the wrapper raises before using it
+        device = torch.device("cuda", 0)
+        cuda_stream = 0
+
+    t = torch.zeros(8 * 8 * 16, dtype=torch.int64)
+    with pytest.raises(Q.QSGError) as e:
+        Q.qsg_sweep_static_scratch(t, t[:64], t[:64], Q.Shape(8, 16, 64, 1, 1), 0, [0.3], 1, 0, 1, stream=_Stream())
+    assert e.value.status == -1

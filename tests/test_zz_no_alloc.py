@@ -29,9 +29,13 @@ def _pack_couplings(J, shape):
     return words
 
 
-@pytest.mark.parametrize("algo,boundary", [(Q.HEATBATH, Q.APBC), (Q.METROPOLIS, Q.PBC)])
-def test_static_scratch_sweep_matches_context_sweep(algo, boundary):
-    shape = Q.Shape(8, 48, 70, 2, 3, algo, boundary)
+# L_tau = 48 runs each slot as one chunk; L_tau = 256 with 12 slots runs 8
+# chunks of 32 planes per slot, so the boundary counters of several chunks,
+# their indexing and the wrap from the last chunk to the first are exercised.
+@pytest.mark.parametrize("algo,boundary,Ltau", [(Q.HEATBATH, Q.APBC, 48), (Q.METROPOLIS, Q.PBC, 48),
+                                                (Q.HEATBATH, Q.PBC, 256), (Q.METROPOLIS, Q.APBC, 256)])
+def test_static_scratch_sweep_matches_context_sweep(algo, boundary, Ltau):
+    shape = Q.Shape(8, Ltau, 70, 2, 3, algo, boundary)
     ladder = np.array([0.24, 0.29, 0.34])
     seed = 2718
     ctx = Q.Context([shape])
@@ -54,16 +58,17 @@ def test_static_scratch_sweep_matches_context_sweep(algo, boundary):
         assert np.array_equal(got, ctx.qsg_get_spins(0)), n
 
 
-def test_static_scratch_sweep_rejects_oversized_and_bad_shapes():
+def test_static_scratch_wrapper_rejects_buffers_that_do_not_fit_the_shape():
+    # the wrapper raises before the C entry point is called, so nothing is launched
     dev = torch.device("cuda")
-    buf = torch.zeros(16, dtype=torch.int64, device=dev)
-    with pytest.raises(Q.QSGError) as e:  # L_tau not a multiple of 16
-        Q.qsg_sweep_static_scratch(buf, buf, buf, Q.Shape(8, 24, 64, 1, 1), 0, [0.3], 1, 0, 1)
-    assert e.value.status == -2
-    with pytest.raises(Q.QSGError) as e:  # more ladder positions than the static table holds
-        Q.qsg_sweep_static_scratch(buf, buf, buf, Q.Shape(8, 16, 64, 1, 129), 0, np.linspace(0.1, 0.5, 129), 1, 0, 1)
-    assert e.value.status in (-1, -2)
-    with pytest.raises(Q.QSGError) as e:  # more slots x chunks than the static counters hold
-        Q.qsg_sweep_static_scratch(buf, buf, buf, Q.Shape(8, 16, 64 * 512, 64, 128), 0,
-                                   np.linspace(0.1, 0.5, 128), 1, 0, 1)
+    shape = Q.Shape(8, 16, 64, 1, 1)
+    spins = torch.zeros(shape.slots * 16 * 64, dtype=torch.int64, device=dev)
+    J = torch.zeros(64, dtype=torch.int64, device=dev)
+    small = torch.zeros(16, dtype=torch.int64, device=dev)
+    for args in ((small, J, J), (spins, small, J), (spins, J, small), (spins.int(), J, J), (spins.cpu(), J, J)):
+        with pytest.raises(Q.QSGError) as e:
+            Q.qsg_sweep_static_scratch(*args, shape, 0, [0.3], 1, 0, 1)
+        assert e.value.status == -1
+    with pytest.raises(Q.QSGError) as e:  # ladder length differs from n_k
+        Q.qsg_sweep_static_scratch(spins, J, J, shape, 0, [0.3, 0.4], 1, 0, 1)
     assert e.value.status == -1
