@@ -296,14 +296,18 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
 /* Tuning options (apply to every group of the context):
  *   QSG_OPT_SWEEP_KERNEL  0 = automatic, 1 = one thread per site and colour
  *                         (two launches per sweep), 2 = fused tau-wavefront
- *                         (one launch per sweep; needs L_tau % 8 == 0)
+ *                         (one launch per sweep; needs L_tau % 16 == 0)
  *   QSG_OPT_CHUNK         tau planes per wavefront work unit (0 = automatic;
- *                         otherwise a multiple of 8 that divides every L_tau)
- *   QSG_OPT_WAVEFRONT_VARIANT  register budget of the wavefront kernel:
- *                         0 = two blocks per SM with the couplings held in
- *                         registers, 1 = three blocks per SM, 2 = two blocks
- *                         per SM with the couplings re-read from shared
- *                         memory; process-wide
+ *                         otherwise a multiple of 16 that divides every L_tau)
+ *   QSG_OPT_WAVEFRONT_VARIANT  form of the wavefront kernel, process-wide:
+ *                         0 = one work unit per block with L compiled in
+ *                         (L = 20, 24; 72 registers, three blocks of 288
+ *                         threads per SM at L = 24), four tau planes per
+ *                         block barrier for heat bath and two for
+ *                         Metropolis; other L use the generic kernel;
+ *                         1 = the same with two planes per barrier; 3 = with
+ *                         four; 2 = the generic kernel (several units per
+ *                         block, L at run time, two blocks per SM)
  *   QSG_OPT_CORR_KERNEL   0 = tensor cores (Gram tiles by tcgen05.mma in FP8,
  *                         exact for +-1 spins), 1 = XOR/popcount on the
  *                         integer pipes
@@ -328,9 +332,20 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         quarter of the chunk length (when that is a multiple
  *                         of 16), scheduled after all other units, so that
  *                         short units fill the last wave of blocks
- * Results do not depend on the options: every kernel produces the same bits. */
+ *   QSG_OPT_WAIT_LIMIT    polls of each bounded device wait of the tensor-core
+ *                         correlator pipeline before it gives up (default
+ *                         2^22, 0..2^30).  A wait that gives up makes every
+ *                         role of the kernel run out its loops without
+ *                         further work and sets the context's device flag:
+ *                         that measurement is not accumulated, and
+ *                         qsg_read_correlators returns QSG_ERR_TIMEOUT from
+ *                         then on (the flag stays set for the context).  A
+ *                         small value is a way to exercise that path; the
+ *                         default never gives up on a working GPU.
+ * Results do not depend on the options (except QSG_OPT_WAIT_LIMIT set too low
+ * for the pipeline to make progress): every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
-       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7, QSG_OPT_TAIL = 8 };
+       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7, QSG_OPT_TAIL = 8, QSG_OPT_WAIT_LIMIT = 9 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

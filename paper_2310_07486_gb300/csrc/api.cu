@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "qsg.h"
 #include "qsg_launch.h"
 
@@ -17,6 +19,13 @@ static std::atomic<unsigned long long> g_launches{0};
 void qsg::count_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 
 namespace {
+
+// NVTX range over one entry point (visible in Nsight timelines; costs nothing
+// when no tool is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 constexpr size_t kAlign = 256;
 constexpr int kMaxA = 16384;               // longest A_i table of the tempering test
@@ -199,6 +208,7 @@ struct qsg_ctx {
     int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 on
     int triples = 1;       // QSG_OPT_ONETIME: 1 with the three-replica sums, 0 without
     int tail = 0;          // QSG_OPT_TAIL: slots swept in quarter-length chunks, last
+    unsigned wait_limit = kDefaultWaitLimit;  // QSG_OPT_WAIT_LIMIT: polls per bounded device wait
     PlanBuffers pb;
     PersistentPlan plan{};
     bool plan_ok = false;
@@ -321,6 +331,7 @@ qsg_status qsg_set_stream(qsg_ctx *ctx, void *cuda_stream) {
 }
 
 qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders) {
+    Range range("qsg_init_samples");
     if (!ctx || !k_ladders) return QSG_ERR_ARG;
     // validate every ladder and build every table before touching the device
     std::vector<std::vector<uint32_t>> thr(ctx->groups.size());
@@ -465,6 +476,7 @@ static qsg_status ensure_graph(qsg_ctx *ctx, bool persistent) {
 }
 
 qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
+    Range range("qsg_sweep");
     if (!ctx || n_sweeps < 0) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
@@ -503,6 +515,7 @@ static qsg_status ensure_energy(qsg_ctx *ctx) {
 }
 
 qsg_status qsg_tempering_swap(qsg_ctx *ctx) {
+    Range range("qsg_tempering_swap");
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     qsg_status s = ensure_energy(ctx);
@@ -513,16 +526,18 @@ qsg_status qsg_tempering_swap(qsg_ctx *ctx) {
 }
 
 qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
+    Range range("qsg_measure_correlators");
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     for (const Group &g : ctx->groups)
         QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->corr_tensor, ctx->triples, ctx->d_err,
-                                     ctx->stream));
+                                     ctx->wait_limit, ctx->stream));
     ctx->n_meas++;
     return QSG_OK;
 }
 
 qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw) {
+    Range range("qsg_read_correlators");
     if (!ctx || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     const Group &g = ctx->groups[group];
@@ -707,7 +722,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         return QSG_OK;
     }
     if (option == QSG_OPT_WAVEFRONT_VARIANT) {
-        if (value < 0 || value > 2) return QSG_ERR_ARG;
+        if (value < 0 || value > 3) return QSG_ERR_ARG;
         g_wavefront_variant = (int)value;
         return QSG_OK;
     }
@@ -742,6 +757,11 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
     if (option == QSG_OPT_TAIL) {
         if (value < 0 || value > (1 << 24)) return QSG_ERR_ARG;
         ctx->tail = (int)value;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_WAIT_LIMIT) {
+        if (value < 0 || value > (1LL << 30)) return QSG_ERR_ARG;
+        ctx->wait_limit = (unsigned)value;
         return QSG_OK;
     }
     if (option == QSG_OPT_CHUNK) {

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(256) k_gram(Group g, int p0, const uint64_t *P
 
 // Equal-time overlap of every replica pair at one ladder position.
 cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int triples,
-                           int *status, cudaStream_t st) {
+                           int *status, unsigned wait_limit, cudaStream_t st) {
     if (tensor && !gram_tc_fits(g)) tensor = 0;  // very long L_tau: integer pipes
     const size_t per_pair = measure_scratch_words_per_pair(g);
     int batch = (int)(scratch_words / per_pair);
@@ -127,7 +127,7 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (tensor) {
-            e = launch_gram_tc(g, p0, np, scratch, status, st);
+            e = launch_gram_tc(g, p0, np, scratch, status, wait_limit, st);
         } else {
             count_launches(1);
             k_gram<<<np * g.R * 64, 256, use_smem ? sh_bytes : 0, st>>>(g, p0, scratch, use_smem);

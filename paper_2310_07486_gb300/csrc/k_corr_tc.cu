@@ -44,7 +44,7 @@ constexpr int kEpilogueWarps = 8;
 constexpr int kEpilogue = 256;               // warps 8-15: two per TMEM lane quadrant
 constexpr int kMmaWarp = 16;
 constexpr int kThreads = 17 * 32;
-constexpr unsigned kSpinLimit = 1u << 22;    // bounded mbarrier waits
+constexpr unsigned kSpinLimit = 1u << 22;    // polls of the wait for issued MMAs before TMEM is freed
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -74,12 +74,12 @@ struct Ctl {
 };
 
 // Wait for the phase of the given parity; false (and the abort flag set) when
-// the limit is reached or another thread has given up already.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort) {
+// `limit` polls are used up or another thread has given up already.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort, unsigned limit) {
     volatile int *ab = abort;
     if (*ab) return false;
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < kSpinLimit; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
                      : "=r"(done)
@@ -218,7 +218,8 @@ __device__ __forceinline__ int exact_f32_to_int(uint32_t bits) {
 
 // P: [sample][Ltau][nwx] transposed bits of the batch (sample = (pair, r, bit)).
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int nabuf, int *status) {
+    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int nabuf, int *status,
+              unsigned wait_limit) {
     extern __shared__ __align__(16) uint8_t dyn_raw[];
     uint8_t *dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
     __shared__ Ctl ctl;
@@ -288,9 +289,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (kc < nc) {
                     bool ok = true;
                     if (!isA)
-                        ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort);
+                        ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort, wait_limit);
                     else if (kc == 0)
-                        ok = mbar_wait(&ctl.aempty[ab], (a_par >> ab) & 1u, &ctl.abort);
+                        ok = mbar_wait(&ctl.aempty[ab], (a_par >> ab) & 1u, &ctl.abort, wait_limit);
                     uint8_t *rowp = isA ? abuf + (size_t)kc * kChunkBytes : sB + (size_t)s * kChunkBytes + row * kChunk;
                     if (ok) expand_word(rowp, wc[kc], t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
                     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int t1 = i * kTile + m;
                 for (int jb = i; jb < nb; ++jb, ++n_t) {
                     const int a = (int)(n_t & 1u);
-                    const bool ok = mbar_wait(&ctl.accfull[a], (n_t >> 1) & 1u, &ctl.abort);
+                    const bool ok = mbar_wait(&ctl.accfull[a], (n_t >> 1) & 1u, &ctl.abort, wait_limit);
                     asm volatile("tcgen05.fence::after_thread_sync;\n");
                     if (ok) {
                         // offsets o = t2 - t1 of this tile lie in [omin, omax]; most
@@ -446,18 +447,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int h = u % nhalf;
             for (int item = 0; item < unit_items(h, nb); ++item) {
                 const int i = item_block(h, item, nb);
-                const bool a_ok = mbar_wait(&ctl.afull[ab], (a_par >> ab) & 1u, &ctl.abort);
+                const bool a_ok = mbar_wait(&ctl.afull[ab], (a_par >> ab) & 1u, &ctl.abort, wait_limit);
                 const uint8_t *sAb = sA + (size_t)ab * nc * kChunkBytes;
                 asm volatile("tcgen05.fence::after_thread_sync;\n");
                 for (int jb = i; jb < nb; ++jb, ++n_t) {
                     const int a = (int)(n_t & 1u);
-                    bool ok = a_ok && mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort);
+                    bool ok = a_ok && mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort, wait_limit);
                     asm volatile("tcgen05.fence::after_thread_sync;\n");
                     for (int kc = 0; kc < nc; ++kc) {
                         const uint32_t abase = smem_u32(sAb + (size_t)kc * kChunkBytes);
                         uint32_t bbase = abase;
                         if (jb != i) {
-                            ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort) && ok;
+                            ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort, wait_limit) && ok;
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
                             bbase = smem_u32(sB + (size_t)bs * kChunkBytes);
                         }
@@ -542,7 +543,8 @@ TcPlan gram_tc_plan(const Group &g) {
 
 bool gram_tc_fits(const Group &g) { return gram_tc_plan(g).nstages >= 2; }
 
-cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st) {
+cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, unsigned wait_limit,
+                           cudaStream_t st) {
     const TcPlan plan = gram_tc_plan(g);
     if (plan.nstages < 2) return cudaErrorInvalidValue;
     const size_t sm = gram_tc_smem_bytes(g, plan.nstages, plan.nabuf);
@@ -557,7 +559,7 @@ cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P
     const long long nunits = (long long)nsamples * ((nb + 1) / 2);
     const int grid = (int)(nunits < nsm ? nunits : nsm);
     count_launches(1);
-    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, plan.nstages, plan.nabuf, status);
+    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, plan.nstages, plan.nabuf, status, wait_limit);
     return cudaGetLastError();
 }
 

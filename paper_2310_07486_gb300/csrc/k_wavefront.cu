@@ -28,70 +28,13 @@
 #include <type_traits>
 
 #include "qsg_launch.h"
+#include "qsg_sweep.cuh"
 
 namespace qsg {
 
 namespace {
 
-constexpr int kRing = 16;  // planes held in shared memory (a power of two)
-
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-struct Thresh {
-    uint32_t t[7];  // Metropolis: t[0..2]; heat bath: t[0..6]; non-increasing
-};
-
-// Bits of the scalar threshold m that the bitsliced count is compared with,
-// as all-ones / all-zero masks, found by a binary search over the monotone
-// table.  Heat bath: m = #{n : u < T[n]} (S = -1 iff n_neg >= m).
-// Metropolis: m = 3 - #{c : u < T[c]} (flip iff n_unsat >= m).
-template <int ALGO>
-__device__ __forceinline__ void threshold_masks(uint32_t u, const Thresh &T, uint32_t &m0, uint32_t &m1,
-                                                uint32_t &m2) {
-    if (ALGO == 0) {
-        const bool a1 = u < T.t[1];
-        const bool a0 = u < (a1 ? T.t[2] : T.t[0]);
-        m2 = 0u;
-        m1 = a1 ? 0u : ~0u;
-        m0 = a0 ? 0u : ~0u;
-    } else {
-        const bool c2 = u < T.t[3];
-        const bool c1 = u < (c2 ? T.t[5] : T.t[1]);
-        const uint32_t t0 = c1 ? (c2 ? T.t[6] : T.t[2]) : (c2 ? T.t[4] : T.t[0]);
-        const bool c0 = u < t0;
-        m2 = c2 ? ~0u : 0u;
-        m1 = c1 ? ~0u : 0u;
-        m0 = c0 ? ~0u : 0u;
-    }
-}
-
-__device__ __forceinline__ uint64_t widen(uint32_t m) { return ((uint64_t)m << 32) | m; }
-
-// One site update on multispin words.  Terms: nr/nl/nu/nd spatial neighbours
-// with couplings jr/jl/ju/jd, ntp/ntm time neighbours (APBC sign folded in).
-template <int ALGO>
-__device__ __forceinline__ uint64_t update_site(uint64_t c, uint64_t nr, uint64_t nl, uint64_t nu, uint64_t nd,
-                                                uint64_t ntp, uint64_t ntm, uint64_t jr, uint64_t jl, uint64_t ju,
-                                                uint64_t jd, uint32_t u, const Thresh &T) {
-    uint64_t b0, b1, b2;
-    uint32_t m0, m1, m2;
-    threshold_masks<ALGO>(u, T, m0, m1, m2);
-    const uint64_t M0 = widen(m0), M1 = widen(m1), M2 = widen(m2);
-    if (ALGO == 0)
-        count6(c ^ nr ^ jr, c ^ nl ^ jl, c ^ nu ^ ju, c ^ nd ^ jd, c ^ ntp, c ^ ntm, b0, b1, b2);
-    else
-        count6(nr ^ jr, nl ^ jl, nu ^ ju, nd ^ jd, ntp, ntm, b0, b1, b2);
-    const uint64_t e0 = b0 | ~M0;
-    const uint64_t e1 = (b1 & ~M1) | (~(b1 ^ M1) & e0);
-    const uint64_t ge = (b2 & ~M2) | (~(b2 ^ M2) & e1);
-    return ALGO == 0 ? (c ^ ge) : ge;
-}
+using namespace sweep;
 
 // Per-thread offsets in the class-split shared-memory plane.
 struct Thr {
@@ -460,7 +403,7 @@ int wavefront_chunk(const Group &g, int requested) {
     return C;
 }
 
-int g_wavefront_variant = 0;  // see launch_wf_slot
+int g_wavefront_variant = 0;  // see launch_sweep_wavefront
 
 int wavefront_units_per_block(const Group &g) {
     const int tpu = g.L * g.L / 2;
@@ -499,19 +442,14 @@ static cudaError_t launch_wf(const Group &g, int C, int tail, const uint32_t *sw
 }
 
 // Registers are allocated per SM sub-partition (16K each), so a block of 9
-// warps (288 threads) fits twice per SM at <= 96 registers and three times at
-// <= 72.  Variant 0 (default): 96 registers with the couplings of the
-// thread's sites held in registers for the whole chunk; variant 1: 72
-// registers (three blocks per SM, with spills); variant 2: 96 registers,
-// couplings re-read from shared memory every step.  Blocks of more than 288
-// threads get 64.
+// warps (288 threads) fits twice per SM at <= 96 registers; the couplings of
+// the thread's sites are held in registers for the whole chunk.  Blocks of
+// more than 288 threads get 64.
 template <int ALGO, int SLOT>
 static cudaError_t launch_wf_slot(const Group &g, int C, int tail, const uint32_t *sb, uint32_t sweep, uint64_t seed,
                                   unsigned *arrivals, cudaStream_t st) {
     const int threads = wavefront_units_per_block(g) * (g.L * g.L / 2);
-    if (threads > 288) return launch_wf<ALGO, SLOT, 64>(g, C, tail, sb, sweep, seed, arrivals, st);
-    if (g_wavefront_variant == 1) return launch_wf<ALGO, SLOT, 72>(g, C, tail, sb, sweep, seed, arrivals, st);
-    if (g_wavefront_variant == 2) return launch_wf<ALGO, SLOT, 96>(g, C, tail, sb, sweep, seed, arrivals, st);
+    if (threads > 288) return launch_wf<ALGO, SLOT, 64, true>(g, C, tail, sb, sweep, seed, arrivals, st);
     return launch_wf<ALGO, SLOT, 96, true>(g, C, tail, sb, sweep, seed, arrivals, st);
 }
 
@@ -531,6 +469,15 @@ static cudaError_t launch_wf_algo(const Group &g, int C, int tail, const uint32_
 
 cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
                                    unsigned *arrivals, int C, int tail, cudaStream_t st) {
+    // one unit per block with the lattice size compiled in (k_sweep_unit.cu)
+    // where that kernel exists, unless the generic kernel is asked for
+    if (g_wavefront_variant != 2 && sweep_unit_supported(g)) {
+        const int ts = tail_slots(g, C, tail);
+        // planes per barrier: the form that compiles with the fewest spills at
+        // 72 registers by default (4 for heat bath, 2 for Metropolis)
+        const int pb = g_wavefront_variant == 1 ? 2 : (g_wavefront_variant == 3 ? 4 : (g.algo == 1 ? 4 : 2));
+        return launch_sweep_unit(g, pb, C, ts > 0 ? C / 4 : C, g.nslots - ts, sweep_base, sweep, seed, arrivals, st);
+    }
     if (g.algo == 0) return launch_wf_algo<0>(g, C, tail, sweep_base, sweep, seed, arrivals, st);
     return launch_wf_algo<1>(g, C, tail, sweep_base, sweep, seed, arrivals, st);
 }
@@ -560,6 +507,10 @@ static cudaError_t launch_persistent_algo(const PersistentPlan &pl, const uint32
     if (e != cudaSuccess) return e;
     int blocks = sms * blocks_per_sm[ALGO];
     if (blocks > pl.total_units) blocks = pl.total_units;
+    // the work queue starts at zero on every launch (the kernel's last block
+    // also resets it, but a launch that did not finish must not leave it set)
+    e = cudaMemsetAsync(pl.queue, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
     count_launches(1);
     k_sweep_persistent<ALGO, SLOT, NREG><<<blocks, THREADS, sm, st>>>(pl.groups, pl.order, pl.prefix, pl.chunk,
                                                                       pl.ngroups, pl.queue, sweep_base, sweep,

@@ -31,12 +31,22 @@ cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed
 // The fused wavefront sweep: C = planes per work unit (0 if the group cannot
 // use this kernel), arrivals = nslots * (L_tau / 4) zeroed counters.
 int wavefront_chunk(const Group &g, int requested);
-extern int g_wavefront_variant;  // 0: register cap for 3 blocks/SM when blocks <= 288 threads; 1: 2 blocks/SM
+// 0: one unit per block where k_sweep_unit exists (four planes per barrier
+// for heat bath, two for Metropolis); 1: two planes per barrier; 3: four;
+// 2: the generic kernel
+extern int g_wavefront_variant;
 // The sweep index is *sweep_base + sweep (sweep_base may be null), so that a
 // captured CUDA graph of several sweeps can be replayed later.  The last
 // `tail` slots (0 = none) run chunks of C / 4 planes after every other unit.
 cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, uint32_t sweep, uint64_t seed,
                                    unsigned *arrivals, int C, int tail, cudaStream_t st);
+// The one-unit-per-block form (k_sweep_unit.cu) for L = 20, 24: slots
+// [0, S1) in chunks of C planes, the others in chunks of C2; 2 or 4 planes
+// per block barrier.
+bool sweep_unit_supported(const Group &g);
+cudaError_t launch_sweep_unit(const Group &g, int planes_per_barrier, int C, int C2, int S1,
+                              const uint32_t *sweep_base, uint32_t sweep, uint64_t seed, unsigned *arrivals,
+                              cudaStream_t st);
 cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st);
 cudaError_t launch_add_word(uint32_t *p, uint32_t value, cudaStream_t st);
 
@@ -62,17 +72,19 @@ cudaError_t launch_tempering(const Group &g, uint32_t m, uint64_t seed, cudaStre
 // Correlator accumulation through the x-packed transposed scratch buffer;
 // tensor = 1 computes the Gram tiles with tcgen05 (k_corr_tc.cu), 0 with
 // XOR/popcount on the integer pipes.  status receives DEVERR_TIMEOUT if a
-// bounded wait of the tensor path gave up.
+// bounded wait of the tensor path gave up (after wait_limit polls).
 // triples = 1 also accumulates the three-replica one-time sums (3 <= R <= 8).
+constexpr unsigned kDefaultWaitLimit = 1u << 22;
 cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_words, int tensor, int triples,
-                           int *status, cudaStream_t st);
+                           int *status, unsigned wait_limit, cudaStream_t st);
 // One-time observable sums of a batch of (w, j) pairs from the transposed scratch.
 cudaError_t launch_onetime(const Group &g, int p0, int np, const uint64_t *P, int triples, cudaStream_t st);
 // FP64 finish of the one-time observables into g.outO and g.outK.
 cudaError_t launch_onetime_finish(const Group &g, long long n_meas, int triples, cudaStream_t st);
 // Tensor-core Gram path over the transposed bits P of a batch: folds every
 // 128 x 128 tile of the Gram matrices into the lag sums.
-cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, cudaStream_t st);
+cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, unsigned wait_limit,
+                           cudaStream_t st);
 bool gram_tc_fits(const Group &g);  // the tensor-core path's shared memory fits one CTA
 
 // FP64 finish into g.outC / g.outQ / g.outP.

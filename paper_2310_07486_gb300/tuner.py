@@ -1,11 +1,12 @@
 """Launch-option autotuner for qsg_sweep.
 
 Every option of ``qsg_set_option`` that shapes the sweep launch (tau chunk per
-work unit, register variant, persistent multi-group launch, CUDA-graph batch,
+work unit, kernel form, persistent multi-group launch, CUDA-graph batch,
 slots swept in shorter chunks at the end of a launch) leaves the sampled bits
 unchanged, so the choice is purely one of speed.  The tuner times each valid
 combination of the first four on the caller's own context with CUDA events on
-the context's stream, then the tail length with the best of them, keeps the
+the context's stream, then the tail lengths with the best launch of each of the
+four fastest chunk lengths, keeps the
 fastest, and caches the choice in a JSON file keyed by the group shapes, the
 device name and the library build.
 
@@ -29,7 +30,8 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 _NAMES = {Q.OPT_CHUNK: "chunk", Q.OPT_WAVEFRONT_VARIANT: "variant", Q.OPT_PERSISTENT: "persistent",
           Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail"}
 DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0}
-TAILS = [0, 16, 24, 32, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
+TAILS = [0, 16, 24, 28, 32, 40, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
+VARIANTS = [0, 1, 2, 3]  # forms of the wavefront kernel (QSG_OPT_WAVEFRONT_VARIANT)
 
 
 def _library_id() -> str:
@@ -61,7 +63,7 @@ def candidates(shapes, sweeps_per_call):
     chunks = candidate_chunks(shapes)
     persistent = [1, 2] if len(shapes) > 1 else [1]
     graph = [0, sweeps_per_call] if sweeps_per_call > 1 else [0]
-    for chunk, variant, pers, gr in itertools.product(chunks, [0, 1, 2], persistent, graph):
+    for chunk, variant, pers, gr in itertools.product(chunks, VARIANTS, persistent, graph):
         yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0}
 
 
@@ -127,9 +129,15 @@ def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=Tr
             table.append((t, cand))
             if verbose:
                 print(f"  {cand} {t:.4f} ms/sweep", flush=True)
-        # second stage: the tail length with the best launch of the first
-        if table:
-            first = min(table, key=lambda tc: tc[0])[1]
+        # second stage: the tail lengths with the best launch of each chunk
+        # length (a longer chunk that fills the last wave badly without a tail
+        # can win with one)
+        best_per_chunk = {}
+        for t, cand in table:
+            c = cand["chunk"]
+            if c not in best_per_chunk or t < best_per_chunk[c][0]:
+                best_per_chunk[c] = (t, cand)
+        for _, first in sorted(best_per_chunk.values(), key=lambda tc: tc[0])[:4]:
             for tail in TAILS[1:]:
                 cand = dict(first, tail=tail)
                 try:

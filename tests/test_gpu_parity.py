@@ -172,11 +172,16 @@ def test_checkpoint_resume_is_bit_exact():
     assert np.array_equal(a.qsg_get_spins(0), b.qsg_get_spins(0))
 
 
-def _sampled_full_size(w, sweeps_before_swap, n_swaps, sample, configs):
+def _sampled_full_size(w, sweeps_before_swap, n_swaps, sample, configs, options=None):
     """Full-size GPU run against one sample simulated alone by the oracle."""
     shape, lad = w.shapes[0], w.ladders[0]
     ctx = Q.Context([shape])
     ctx.qsg_init_samples(w.seed, [lad])
+    for opt, val in (options or {}).items():
+        ctx.qsg_set_option(opt, val)
+    if options:
+        # the graph batch must be what the sweeps replay
+        assert sweeps_before_swap % options.get(Q.OPT_GRAPH, 1) == 0
     orc = oracle.OracleGroup(shape.L, shape.Ltau, 1, shape.n_replicas, shape.n_k, algo=shape.algo,
                              boundary=shape.boundary, first_sample=sample)
     orc.init(w.seed, lad)
@@ -196,6 +201,8 @@ def _sampled_full_size(w, sweeps_before_swap, n_swaps, sample, configs):
         C, Qs = orc.measure_one(0, r, j)
         assert np.array_equal(gpu["C_raw"][r, sample, j], C)
         assert np.array_equal(gpu["Q2_raw"][r, sample, j], Qs)
+    if options:
+        ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, 0)
     # properties that hold for every sample at any size
     assert np.all(gpu["C"][..., 0] == 1.0) and np.all(gpu["Q2"][..., 0] == 1.0)
     assert np.all(np.abs(gpu["C"]) <= 1.0) and np.all((gpu["Q2"] >= 0) & (gpu["Q2"] <= 1.0))
@@ -210,6 +217,17 @@ def test_mid_scale_sampled():
 def test_largest_sampled_in_bench_configuration():
     w = workloads.largest()
     _sampled_full_size(w, 2, 1, sample=77, configs=[(1, 5)])
+
+
+def test_largest_sampled_with_the_benchmark_launch_options():
+    """L = 24, L_tau = 2048, 128 samples x 4 replicas x 32 k, heat bath, in the
+    launch configuration the benchmark times: one unit per block, chunks of 512
+    planes with the last 32 slots in chunks of 128, and one CUDA-graph replay of
+    30 sweeps, then a tempering step and a measurement; one sample against the
+    oracle."""
+    w = workloads.largest()
+    options = {Q.OPT_CHUNK: 512, Q.OPT_TAIL: 32, Q.OPT_GRAPH: 30, Q.OPT_WAVEFRONT_VARIANT: 0}
+    _sampled_full_size(w, 30, 1, sample=101, configs=[(2, 17)], options=options)
 
 
 @pytest.mark.parametrize("L,Ltau,chunk", [(8, 16, 16), (8, 32, 16), (8, 64, 32), (8, 32, 0), (6, 32, 16),
@@ -248,12 +266,13 @@ def test_reference_and_wavefront_kernels_agree_at_mid_scale():
     assert np.array_equal(out[0], out[1])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 @pytest.mark.parametrize("L,R,algo", [(8, 2, Q.HEATBATH), (24, 2, Q.METROPOLIS), (24, 3, Q.HEATBATH),
-                                      (32, 2, Q.HEATBATH), (6, 4, Q.METROPOLIS)])
+                                      (20, 2, Q.HEATBATH), (20, 3, Q.METROPOLIS), (32, 2, Q.HEATBATH),
+                                      (6, 4, Q.METROPOLIS)])
 def test_wavefront_register_variants_match_oracle(variant, L, R, algo):
-    """Every kernel variant (one or two replicas per thread, register budgets)
-    gives the oracle's bits."""
+    """Every form of the wavefront kernel (one unit per block with two or four
+    planes per barrier, the generic kernel) gives the oracle's bits."""
     shape = Q.Shape(L, 16, 70, R, 2, algo, Q.APBC)
     ctx, orc = _pair(shape, np.array([0.27, 0.3]), seed=41)
     ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, variant)
@@ -495,3 +514,31 @@ def test_wavefront_tail_slots_in_short_chunks_match_oracle(Ltau, chunk, tail):
     ctx.qsg_sweep(2)
     orc.sweep(2)
     assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+
+
+@pytest.mark.parametrize("L", [20, 24])
+@pytest.mark.parametrize("algo,boundary", [(Q.METROPOLIS, Q.APBC), (Q.HEATBATH, Q.PBC)])
+@pytest.mark.parametrize("Ltau,chunk,tail,variant", [(16, 16, 0, 0), (64, 16, 0, 3), (64, 32, 0, 1),
+                                                     (128, 64, 2, 0), (256, 128, 3, 1), (256, 64, 2, 3)])
+def test_unit_kernel_chunks_and_tails_match_oracle(L, algo, boundary, Ltau, chunk, tail, variant):
+    """The one-unit-per-block sweep (k_sweep_unit) against the oracle: single
+    and several chunks per slot, tails swept in quarter-length chunks down to
+    16 planes, two and four planes per barrier, both boundaries."""
+    shape = Q.Shape(L, Ltau, 66, 2, 2, algo, boundary)
+    ctx, orc = _pair(shape, np.array([0.26, 0.33]), seed=53)
+    ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, variant)
+    try:
+        ctx.qsg_set_option(Q.OPT_CHUNK, chunk)
+        ctx.qsg_set_option(Q.OPT_TAIL, tail)
+        for n in (1, 2):
+            ctx.qsg_sweep(n)
+            orc.sweep(n)
+            assert np.array_equal(_gpu_spins(ctx, shape), orc.spins()), n
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        ctx.qsg_set_option(Q.OPT_GRAPH, 2)
+        ctx.qsg_sweep(4)
+        orc.sweep(4)
+        assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    finally:
+        ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, 0)
