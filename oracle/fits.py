@@ -5,15 +5,14 @@ of Sect. "On the magnetic susceptibilities".
 TEST INFRASTRUCTURE ONLY: loaded by the tests and nothing else.  It shares no
 code with the library's fits (csrc/fits.cpp).
 
-The paper does not name its minimiser.  Both sides read it as Marquardt's
-damped Gauss-Newton (Levenberg-Marquardt): damping lambda = 1e-3 to start,
-the normal matrix's diagonal scaled by (1 + lambda), lambda x10 after a
-rejected step (chi2 not lower, or a decay length not positive), /10 after an
-accepted one (not below 1e-15); stop when an accepted step is below 1e-14 of
-every parameter, when chi2 falls by less than 1e-15 of itself, after 2000
-iterations or when lambda exceeds 1e30.  Following the same iteration from
-the same start, two-exponential fits reach the same one of their several
-minima on both sides.
+The paper does not name its minimiser; what it defines is the minimum of
+chi2 over the model's parameters.  This oracle reaches it with scipy's
+trust-region-reflective least squares (scipy.optimize.least_squares,
+method "trf"), with every decay length bounded to (0, 10 L_tau] and
+tolerances of 1e-15: a different algorithm from the library's, so that the
+two agree on the minimum and not on an iteration path.  One-exponential fits
+have a single minimum in that box; two-exponential fits can have several, and
+there the two sides may end at different ones.
 
 Steps, in the paper's order, for one sample at one k given the correlators of
 its R replicas at lags 0 .. L_tau/2:
@@ -94,59 +93,37 @@ def _loglin_guess(tau, y):
     return (float(y[ok][0]) if ok.any() else 1.0), max(1.0, (tau[-1] - tau[0]) / 2)
 
 
-def _lsq(model, jac, p0, tau, y, s, valid):
-    """Levenberg-Marquardt minimisation of sum ((model - y) / s)^2."""
-    w = 1.0 / s ** 2
+def _lsq(model, jac, p0, tau, y, s, eta_index, Ltau):
+    """Minimum of sum ((model - y) / s)^2 with the decay lengths p[eta_index]
+    in (0, 10 L_tau]; parameter errors from (J^T W J)^-1 at the minimum."""
+    from scipy.optimize import least_squares
 
-    def chi2_of(p):
-        return float((w * (model(p, tau) - y) ** 2).sum())
+    def res(p):
+        return (model(p, tau) - y) / s
 
-    def normal(p):
-        J = jac(p, tau)
-        r = model(p, tau) - y
-        return (J * w[:, None]).T @ J, (J * w[:, None]).T @ r
+    def jres(p):
+        return jac(p, tau) / s[:, None]
 
-    p = np.array(p0, dtype=np.float64)
-    chi2 = chi2_of(p)
-    lam = 1e-3
-    A, g = normal(p)
-    it = 0
-    while it < 2000 and lam < 1e30:
-        it += 1
-        diag = np.where(np.diag(A) > 0, np.diag(A), 1.0)
-        M = A + lam * np.diag(diag)
-        try:
-            step = np.linalg.solve(M, -g)
-        except np.linalg.LinAlgError:
-            lam *= 10.0
-            continue
-        trial = p + step
-        c2 = chi2_of(trial) if valid(trial) else math.inf
-        if not c2 < chi2:
-            lam *= 10.0
-            continue
-        small = bool(np.all(np.abs(step) <= 1e-14 * (np.abs(p) + 1e-14)))
-        flat = chi2 - c2 <= 1e-15 * chi2
-        p, chi2 = trial, c2
-        lam = max(lam * 0.1, 1e-15)
-        A, g = normal(p)
-        if small or flat:
-            break
+    lo = np.full(len(p0), -np.inf)
+    hi = np.full(len(p0), np.inf)
+    lo[eta_index] = 1e-12
+    hi[eta_index] = 10.0 * Ltau
+    x0 = np.clip(np.asarray(p0, dtype=np.float64), lo + 1e-12, hi)
+    r = least_squares(res, x0, jac=jres, method="trf", bounds=(lo, hi), xtol=1e-15, ftol=1e-15, gtol=1e-15,
+                      max_nfev=20000)
+    p = r.x
+    chi2 = float((res(p) ** 2).sum())
+    Jw = jres(p)
     try:
-        err = np.sqrt(np.abs(np.diag(np.linalg.inv(A))))
+        err = np.sqrt(np.abs(np.diag(np.linalg.inv(Jw.T @ Jw))))
     except np.linalg.LinAlgError:
         err = np.full(len(p), np.nan)
     return p, err, chi2
 
 
-def fit_C(C, s, Ltau, zeta):
-    """Decay length eta of the odd correlator; dict with the window and fit."""
-    tw = window(C, s, Ltau)
-    out = dict(tau_w=tw if tw is not None else Ltau // 2, ok=False, eta=np.nan, eta_err=np.nan, B=np.nan,
-               chi2dof=np.nan, tau_min=0)
-    if tw is None:
-        return out  # eta > L_tau: not estimated
-
+def fit_C_at(C, s, Ltau, zeta, tmin, tw):
+    """The C fit on [tmin, tw]: (chi2, dof, params (B, eta), errors), or None
+    when fewer than three lags carry weight."""
     def model(p, t):
         B, eta = p
         return B * (np.exp(-t / eta) + zeta * np.exp(-(Ltau - t) / eta))
@@ -156,16 +133,30 @@ def fit_C(C, s, Ltau, zeta):
         e1, e2 = np.exp(-t / eta), np.exp(-(Ltau - t) / eta)
         return np.stack([e1 + zeta * e2, B * (e1 * t + zeta * e2 * (Ltau - t)) / eta ** 2], axis=1)
 
+    tau = np.arange(tmin, tw + 1)
+    tau = tau[s[tau] > 0]
+    dof = len(tau) - 2
+    if dof < 1:
+        return None
+    B0, eta0 = _loglin_guess(tau.astype(float), C[tau])
+    p, err, chi2 = _lsq(model, jac, np.array([B0, min(eta0, 10.0 * Ltau)]), tau.astype(float), C[tau], s[tau],
+                        [1], Ltau)
+    return chi2, dof, p, err
+
+
+def fit_C(C, s, Ltau, zeta):
+    """Decay length eta of the odd correlator; dict with the window and fit."""
+    tw = window(C, s, Ltau)
+    out = dict(tau_w=tw if tw is not None else Ltau // 2, ok=False, eta=np.nan, eta_err=np.nan, B=np.nan,
+               chi2dof=np.nan, tau_min=0)
+    if tw is None:
+        return out  # eta > L_tau: not estimated
     tmin = max(1, tw // 10)
     while True:
-        tau = np.arange(tmin, tw + 1)
-        tau = tau[s[tau] > 0]
-        dof = len(tau) - 2
-        if dof < 1:
+        r = fit_C_at(C, s, Ltau, zeta, tmin, tw)
+        if r is None:
             return out
-        B0, eta0 = _loglin_guess(tau.astype(float), C[tau])
-        p, err, chi2 = _lsq(model, jac, np.array([B0, min(eta0, 10.0 * Ltau)]), tau.astype(float), C[tau], s[tau],
-                            lambda q: 0 < q[1] <= 10.0 * Ltau)
+        chi2, dof, p, err = r
         if chi2 / dof < C_CHI2:
             if p[1] > Ltau:
                 return out  # eta beyond L_tau: not estimated
@@ -175,9 +166,10 @@ def fit_C(C, s, Ltau, zeta):
         tmin += 1
 
 
-def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl, Ltau):
-    """Q2 = Q_pl + sum of nexp exponentials, tau_min from 1 up until
-    chi2/dof < 0.5; returns (chi2/dof, params, errors, tau_min) or None."""
+def fit_Q_at(Q, s, Ltau, tmin, tw, nexp, qpl, free_pl):
+    """Q2 = Q_pl + sum of nexp exponentials on [tmin, tw] (Q_pl a parameter
+    when free_pl): (chi2, dof, params, errors), or None without a degree of
+    freedom.  Parameters: [Q_pl,] B_1, eta_1[, B_2, eta_2]."""
     def split(p):
         if free_pl:
             return p[0], p[1:]
@@ -196,27 +188,33 @@ def _fit_Q_terms(Q, s, lo_max, tw, nexp, qpl, free_pl, Ltau):
         return np.stack(cols, axis=1)
 
     npar = 2 * nexp + (1 if free_pl else 0)
-    for tmin in range(1, lo_max + 1):
-        tau = np.arange(tmin, tw + 1)
-        tau = tau[s[tau] > 0]
-        dof = len(tau) - npar
-        if dof < 1:
+    tau = np.arange(tmin, tw + 1)
+    tau = tau[s[tau] > 0]
+    dof = len(tau) - npar
+    if dof < 1:
+        return None
+    t = tau.astype(float)
+    base = qpl if not free_pl else float(Q[tau[-1]])
+    B0, eta0 = _loglin_guess(t, Q[tau] - base)
+    q0 = [B0, eta0] if nexp == 1 else [0.5 * B0, 2.0 * eta0, 0.5 * B0, 0.5 * eta0]
+    p0 = np.array(([base] if free_pl else []) + q0)
+    off = 1 if free_pl else 0
+    p0[off + 1::2] = np.minimum(p0[off + 1::2], 10.0 * Ltau)
+    p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau], list(range(off + 1, len(p0), 2)), Ltau)
+    return chi2, dof, p, err
+
+
+def _fit_Q_terms(Q, s, tw, nexp, qpl, free_pl, Ltau):
+    """tau_min from 1 up until chi2/dof < 0.5; returns (chi2/dof, params,
+    errors, tau_min) or None."""
+    off = 1 if free_pl else 0
+    for tmin in range(1, tw + 1):
+        r = fit_Q_at(Q, s, Ltau, tmin, tw, nexp, qpl, free_pl)
+        if r is None:
             return None
-        t = tau.astype(float)
-        base = qpl if not free_pl else float(Q[tau[-1]])
-        B0, eta0 = _loglin_guess(t, Q[tau] - base)
-        if nexp == 1:
-            q0 = [B0, eta0]
-        else:
-            q0 = [0.5 * B0, 2.0 * eta0, 0.5 * B0, 0.5 * eta0]
-        p0 = np.array(([base] if free_pl else []) + q0)
-        off = 1 if free_pl else 0
-        p0[off + 1::2] = np.minimum(p0[off + 1::2], 10.0 * Ltau)
-        p, err, chi2 = _lsq(model, jac, p0, t, Q[tau], s[tau],
-                            lambda q: bool(np.all((q[off + 1::2] > 0) & (q[off + 1::2] <= 10.0 * Ltau))))
-        etas = p[off + 1::2]
+        chi2, dof, p, err = r
         if chi2 / dof < Q_CHI2:
-            if np.any(etas > Ltau):
+            if np.any(p[off + 1::2] > Ltau):
                 return None  # a decay length beyond L_tau: this model is not estimated
             return chi2 / dof, p, err, int(tmin)
     return None
@@ -234,7 +232,7 @@ def fit_Q2(Q, s, Ltau):
                eta_e=np.nan, eta_e_err=np.nan, eta_2=np.nan, chi2dof=np.nan, tau_min=0)
     best = None
     for nexp in (1, 2):
-        r = _fit_Q_terms(Q, s, tw, tw, nexp, qpl, free_pl=not pl_ok, Ltau=Ltau)
+        r = _fit_Q_terms(Q, s, tw, nexp, qpl, free_pl=not pl_ok, Ltau=Ltau)
         if r is not None and (best is None or r[0] < best[1][0]):
             best = (nexp, r)
     if best is None:

@@ -249,3 +249,181 @@ def judge(E_bins, q_bins, n_last=3, n_sigma=2.0):
                 out[b] = m
                 break
     return out
+
+
+# --------------------------------------------------------------------------
+# element-wise error bounds of the FP32 / BF16 arithmetic, for comparing a
+# single-precision implementation with the FP64 definitions above
+#
+# Standard forward error analysis (Higham, "Accuracy and Stability of
+# Numerical Algorithms", 2nd ed., Sect. 3.1): an n-term sum or dot product
+# evaluated in any order with fused multiply-adds in a format of unit roundoff
+# u satisfies |fl(s) - s| <= gamma_n * sum |terms|, gamma_n = n u / (1 - n u).
+# Errors of the inputs add through the Lipschitz constant of each step
+# (|W| for a matrix product, 1 for ReLU, p for exp).  A ReLU mask is
+# ambiguous where |z| does not exceed the bound on z's error: there the
+# single-precision result may take either branch, and the bound allows both.
+# The bounds are first order; they are doubled to cover the neglected
+# second-order terms and the roundings of single operations not itemised
+# (the max of the softmax, the constant 1/B, each final store).
+# --------------------------------------------------------------------------
+U32 = 2.0 ** -24  # unit roundoff of IEEE binary32
+
+
+def gamma(n, u=U32):
+    return n * u / (1.0 - n * u)
+
+
+def prop(E, A):
+    """Error that input errors E (rows: samples) carry through a product with
+    A = |weights|: at most E @ A."""
+    return E @ A
+
+
+def _tiles(B, tile=16):
+    """Terms of a batch sum computed as per-tile sums of <= `tile` samples,
+    then the tile sums in order: at most tile + number of tiles roundings."""
+    return min(B, tile) + (B + tile - 1) // tile
+
+
+def fp32_forward_bound(theta, X):
+    """(y, e_y, and per-layer (z, e_z)) for the FP32 forward pass: e bounds
+    |y_fp32 - y| element-wise."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    X = np.asarray(X, dtype=np.float64)
+    z1 = X @ W1.T + b1
+    e1 = gamma(W1.shape[1] + 1) * (np.abs(X) @ np.abs(W1).T + np.abs(b1))
+    h1 = np.maximum(z1, 0)
+    z2 = h1 @ W2.T + b2
+    e2 = gamma(W2.shape[1] + 1) * (h1 @ np.abs(W2).T + np.abs(b2)) + prop(e1, np.abs(W2).T)
+    h2 = np.maximum(z2, 0)
+    y = h2 @ W3.T + b3
+    ey = gamma(W3.shape[1] + 1) * (h2 @ np.abs(W3).T + np.abs(b3)) + prop(e2, np.abs(W3).T)
+    return y, 2.0 * ey, (z1, 2.0 * e1, z2, 2.0 * e2)
+
+
+def grad_error_bound(theta, X, T, tile=16):
+    """Element-wise bounds on |loss_fp32 - loss| and |g_fp32 - g| for the FP32
+    loss and backpropagation of `loss_and_grad` over one batch (per-tile sums
+    of <= 16 samples, then the tiles in order).  Returns (loss_bound, g_bound)."""
+    W1, b1, W2, b2, W3, b3 = unpack(theta)
+    X = np.asarray(X, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    B = T.shape[0]
+    nb = _tiles(B, tile)
+    y, ey, (z1, e1, z2, e2) = fp32_forward_bound(theta, X)
+    h1, h2 = np.maximum(z1, 0), np.maximum(z2, 0)
+    # softmax, loss and dL/dy
+    a = y[:, :32]
+    mx = a.max(axis=1, keepdims=True)
+    lse = np.log(np.exp(a - mx).sum(axis=1, keepdims=True))
+    logp = a - mx - lse
+    p = np.exp(logp)
+    t = T[:, :32]
+    tsum = t.sum(axis=1, keepdims=True)
+    emax = ey[:, :32].max(axis=1, keepdims=True)
+    # logp: y, the max and the log-sum (each shifted by <= emax, the sum of 32
+    # exponentials of <= 2 ulp each), two subtractions
+    e_lse = 2.0 * emax + gamma(34) + 2.0 * U32 * np.abs(lse)
+    e_logp = ey[:, :32] + emax + e_lse + 2.0 * U32 * (np.abs(a - mx) + np.abs(lse))
+    e_p = p * (e_logp + 3.0 * U32)
+    e_tsum = gamma(32) * tsum
+    dy = np.zeros_like(y)
+    e_dy = np.zeros_like(y)
+    dy[:, :32] = (p * tsum - t) / B
+    e_dy[:, :32] = (e_p * tsum + p * e_tsum + 3.0 * U32 * (p * tsum + t)) / B + U32 * np.abs(dy[:, :32])
+    r = y[:, 32] - T[:, 32]
+    dy[:, 32] = 2 * r / B
+    e_dy[:, 32] = 2.0 * (ey[:, 32] + U32 * np.abs(r)) / B + 2.0 * U32 * np.abs(dy[:, 32])
+    M_dy = np.abs(dy) + e_dy
+    # loss = sum over tiles of (sum over the tile of ce + r^2) / B
+    ce = -(t * logp).sum(axis=1)
+    e_ce = (t * e_logp).sum(axis=1) + gamma(33) * (t * np.abs(logp)).sum(axis=1)
+    e_r = ey[:, 32] + U32 * np.abs(r)
+    per = (e_ce + 2.0 * np.abs(r) * e_r + 2.0 * U32 * r * r) / B
+    loss_bound = per.sum() + gamma(nb + 1) * (np.abs(ce) + r * r).sum() / B
+
+    def outer(d, e_d, h, e_h):
+        # sum over the batch of d (x) h: rounding, then the inputs' errors
+        Md = np.abs(d) + e_d
+        return gamma(nb) * Md.T @ (np.abs(h) + e_h) + e_d.T @ np.abs(h) + np.abs(d).T @ e_h
+
+    def colsum(d, e_d):
+        return gamma(nb) * (np.abs(d) + e_d).sum(0) + e_d.sum(0)
+
+    def relu_back(dh, e_dh, z, e_z):
+        ambiguous = np.abs(z) <= e_z
+        dz = dh * (z > 0)
+        e_dz = np.where(ambiguous, np.abs(dh) + e_dh, np.where(z > 0, e_dh, 0.0))
+        return dz, e_dz
+
+    gW3 = outer(dy, e_dy, h2, e2)
+    gb3 = colsum(dy, e_dy)
+    dh2 = dy @ W3
+    e_dh2 = gamma(33) * M_dy @ np.abs(W3) + prop(e_dy, np.abs(W3))
+    dz2, e_dz2 = relu_back(dh2, e_dh2, z2, e2)
+    gW2 = outer(dz2, e_dz2, h1, e1)
+    gb2 = colsum(dz2, e_dz2)
+    dh1 = dz2 @ W2
+    e_dh1 = gamma(W2.shape[0]) * (np.abs(dz2) + e_dz2) @ np.abs(W2) + prop(e_dz2, np.abs(W2))
+    dz1, e_dz1 = relu_back(dh1, e_dh1, z1, e1)
+    gW1 = outer(dz1, e_dz1, X, np.zeros_like(X))
+    gb1 = colsum(dz1, e_dz1)
+    return 2.0 * float(loss_bound), 2.0 * pack([gW1, gb1, gW2, gb2, gW3, gb3])
+
+
+def adam_step_bound(theta, m, v, e_m, e_v, g, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+    """One Adam step in FP64 from the FP32 state (theta, m, v, the same
+    gradient g) with element-wise bounds: returns (theta', m', v', e_m', e_v',
+    e_theta) where e_m, e_v bound the single-precision moments' accumulated
+    errors and e_theta bounds |theta'_fp32 - theta'| (given equal theta and g).
+    Each FP32 operation rounds once (<= u relative); the factor 1 - b^t and
+    the learning rate are rounded to FP32 once each."""
+    g = np.asarray(g, dtype=np.float64)
+    m1 = b1 * m + (1 - b1) * g
+    v1 = b2 * v + (1 - b2) * g * g
+    e_m1 = b1 * e_m + 3.0 * U32 * (b1 * np.abs(m) + (1 - b1) * np.abs(g))
+    e_v1 = b2 * e_v + 4.0 * U32 * (b2 * v + (1 - b2) * g * g)
+    c1, c2 = 1 - b1 ** t, 1 - b2 ** t
+    mh, vh = m1 / c1, v1 / c2
+    den = np.sqrt(vh) + eps
+    step = lr * mh / den
+    # relative errors: the quotient m^ (moment and factor), the square root of
+    # v^ (half of v^'s relative error), the sum with eps, the final quotient
+    # and product, the learning rate
+    e_mh = e_m1 / c1 + 2.0 * U32 * np.abs(mh)
+    rel_den = (0.5 * (e_v1 / np.maximum(v1, 1e-300) + 2.0 * U32) * np.sqrt(vh) + U32 * den) / den
+    e_step = lr * e_mh / den + np.abs(step) * (rel_den + 4.0 * U32)
+    theta1 = theta - step
+    e_theta = e_step + U32 * np.abs(theta1)
+    return theta1, m1, v1, e_m1, e_v1, 2.0 * e_theta
+
+
+def _bf16_interval(lo, hi):
+    """Every bfloat16 value that rounding (to nearest even) of an FP32 value in
+    [lo, hi] can give, as an interval; the endpoints are first widened by one
+    FP32 ulp for their own conversion to FP32."""
+    lo = lo - np.abs(lo) * 2.0 ** -23
+    hi = hi + np.abs(hi) * 2.0 ** -23
+    return to_bf16(lo), to_bf16(hi)
+
+
+def forward_bf16_interval(theta, X):
+    """Interval [lo, hi] holding every output the BF16 inference can give:
+    BF16 weights, inputs and hidden activations (round to nearest even), FP32
+    accumulation with fused multiply-adds (products of two BF16 values are
+    exact in FP32; each sum errs by <= gamma_n sum |terms|), outputs in FP32.
+    An activation whose FP32 value may fall on either side of a BF16 rounding
+    boundary takes both neighbours, and the spread is carried forward."""
+    W1, b1, W2, b2, W3, b3 = [to_bf16(p) for p in unpack(theta)]
+    h = to_bf16(X)
+    lo = hi = h
+    for W, b, last in ((W1, b1, False), (W2, b2, False), (W3, b3, True)):
+        mid, rad = (lo + hi) / 2, (hi - lo) / 2
+        c = mid @ W.T + b
+        mag = np.maximum(np.abs(lo), np.abs(hi)) @ np.abs(W).T + np.abs(b)
+        r = prop(rad, np.abs(W).T) + 2.0 * gamma(W.shape[1] + 1) * mag
+        zlo, zhi = c - r, c + r
+        if last:
+            return zlo - 2.0 * U32 * np.abs(zlo), zhi + 2.0 * U32 * np.abs(zhi)
+        lo, hi = _bf16_interval(np.maximum(zlo, 0), np.maximum(zhi, 0))

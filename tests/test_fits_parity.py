@@ -1,12 +1,20 @@
-"""The library's correlation-length fits (qsg_fit_correlators, host FP64)
-against the fit oracle on seeded synthetic replica correlators: identical
-windows, lags and model choices, fitted values to 1e-6 relative (the same
-Levenberg-Marquardt iteration written twice, stopping at the same minimum),
-parameter errors to 1e-4.  Where a Q2 fit is ill-conditioned (a parameter not
-determined to a quarter of its size) its end point is not unique and the two
-sides may accept different tau_min; there the library's result is checked
-for validity instead (its chi2/dof below the threshold, a decay length in
-(0, L_tau])."""
+"""The library's correlation-length fits (qsg_fit_correlators, host FP64,
+Levenberg-Marquardt) against the fit oracle (scipy's trust-region-reflective
+least squares: an independent route to the same minimum) on seeded synthetic
+replica correlators and on GPU correlators.
+
+Windows, the plateau and its acceptance involve no minimiser: identical.
+Where both sides accept a fit at the same tau_min (and number of terms), they
+found the same minimum: the parameters agree to 1 % of their statistical
+error, chi2 to 1e-4 in absolute chi2 units (a chi2 difference d means
+parameters about sqrt(d) error bars apart, so 1e-4 is 0.01 of an error bar)
+and the errors to 1e-3 relative (errors come from (J^T W J)^-1 at two
+minimiser end points a fraction of an error bar apart).  Where they stop at different tau_min -- a two-exponential fit with
+several minima, or chi2/dof at a threshold within the minimisers' tolerance
+-- the library's result is checked for validity instead: it meets the
+acceptance rule, its decay length lies in (0, L_tau], and its chi2 is no
+worse than the oracle's minimum for the same lags and model (by at most
+1e-4 in chi2 units)."""
 from __future__ import annotations
 
 import numpy as np
@@ -17,12 +25,10 @@ from paper_2310_07486_gb300 import qsg as Q
 
 pytestmark = pytest.mark.gpu  # calls into the compiled library
 
-RTOL = 1e-6
-# Parameter errors come from (J^T W J)^-1; for two-exponential fits its
-# condition number reaches 1e10 and more, so the two sides' different
-# summation orders (1e-16 relative in J^T W J) show up at up to ~1e-5 there.
-RTOL_ERR = 1e-4
-INT_FIELDS = ("C_ok", "C_tau_w", "C_tau_min", "Q_ok", "Q_tau_w", "Q_tau_min", "Q_n_exp", "plateau_ok")
+PAR_SIGMAS = 0.01   # parameter agreement, in units of the oracle's statistical error
+CHI2_ATOL = 1e-4    # chi2 units: 0.01 of an error bar
+ERR_RTOL = 1e-3
+INT_FIELDS = ("C_tau_w", "Q_tau_w", "plateau_ok")
 
 
 def _synthetic(rng, R, n, Ltau, zeta):
@@ -53,48 +59,86 @@ def _synthetic(rng, R, n, Ltau, zeta):
     return C, Q2
 
 
-def _ill_conditioned(lib_res, q):
-    """A Q2 fit whose parameters are not determined to better than a quarter of
-    their size (a five-parameter fit on a few lags, a free plateau): its end
-    point is not unique, so rounding differences between platforms may move
-    the first accepted tau_min."""
-    rel = []
-    for v, e in ((q["Q_pl"], q["Q_pl_err"]), (q["eta_e"], q["eta_e_err"]),
-                 (lib_res["Q_pl"], lib_res["Q_pl_err"]), (lib_res["eta_e"], lib_res["eta_e_err"])):
-        if np.isfinite(v) and np.isfinite(e) and v != 0:
-            rel.append(abs(e / v))
-    return bool(rel) and max(rel) > 0.25
+def _close(a, b, rtol):
+    return abs(a - b) <= rtol * max(abs(b), 1e-300)
 
 
-def _compare(lib_res, orc_res, Ltau=None):
+def _dof(tmin, tw, s, npar):
+    t = np.arange(tmin, tw + 1)
+    return int((s[t] > 0).sum()) - npar
+
+
+def _same_minimum(pairs):
+    """pairs of (library value, oracle value, oracle error)."""
+    for a, b, e in pairs:
+        if np.isfinite(e) and e > 0:
+            assert abs(a - b) <= PAR_SIGMAS * e, (a, b, e)
+        else:
+            assert _close(a, b, 1e-6), (a, b)
+
+
+def _compare(lib_res, orc_res, C_reps, Q_reps, Ltau, boundary):
+    """True when both sides ended at the same minimum of every fit."""
     c, q = orc_res["C"], orc_res["Q2"]
-    want = dict(C_ok=int(c["ok"]), C_tau_w=c["tau_w"], C_tau_min=c["tau_min"], Q_ok=int(q["ok"]),
-                Q_tau_w=q["tau_w"], Q_tau_min=q["tau_min"], Q_n_exp=q["n_exp"], plateau_ok=int(q["plateau_ok"]))
-    q_unique = True
-    if (lib_res["Q_tau_min"], lib_res["Q_n_exp"], lib_res["Q_ok"]) != (q["tau_min"], q["n_exp"], int(q["ok"])) \
-            and _ill_conditioned(lib_res, q):
-        # several outcomes are correct: the library's must be a valid one
-        q_unique = False
-        if lib_res["Q_ok"]:
-            assert lib_res["Q_chi2dof"] < 0.5 and 1 <= lib_res["Q_tau_min"] <= lib_res["Q_tau_w"]
-            assert 0 < lib_res["eta_e"] and (Ltau is None or lib_res["eta_e"] <= Ltau)
-    for f in INT_FIELDS:
-        if not q_unique and f in ("Q_ok", "Q_tau_min", "Q_n_exp"):
-            continue
-        assert lib_res[f] == want[f], (f, lib_res[f], want[f])
-    pairs = [("plateau_chi2dof", q["plateau_chi2dof"])]
-    if q["plateau_ok"] or q_unique:
-        pairs += [("Q_pl", q["Q_pl"]), ("Q_pl_err", q["Q_pl_err"])]
-    if c["ok"]:
-        pairs += [("eta", c["eta"]), ("eta_err", c["eta_err"]), ("C_amp", c["B"]), ("C_chi2dof", c["chi2dof"])]
-    if q["ok"] and q_unique:
-        pairs += [("eta_e", q["eta_e"]), ("eta_e_err", q["eta_e_err"]), ("Q_chi2dof", q["chi2dof"])]
-        if q["n_exp"] == 2:
-            pairs += [("eta_2", q["eta_2"])]
-    for f, v in pairs:
-        tol = RTOL_ERR if f.endswith("_err") else RTOL
-        assert abs(lib_res[f] - v) <= tol * max(abs(v), 1e-300), (f, lib_res[f], v)
-    return q_unique
+    assert (lib_res["C_tau_w"], lib_res["Q_tau_w"], lib_res["plateau_ok"]) == (c["tau_w"], q["tau_w"],
+                                                                                int(q["plateau_ok"]))
+    assert _close(lib_res["plateau_chi2dof"], q["plateau_chi2dof"], 1e-9)
+    Cm, sc = ofits.replica_stats(C_reps)
+    Qm, sq = ofits.replica_stats(Q_reps)
+    zeta = -1.0 if boundary == Q.APBC else 1.0
+    same = True
+    # odd correlator
+    if (lib_res["C_ok"], lib_res["C_tau_min"]) == (int(c["ok"]), c["tau_min"]):
+        if c["ok"]:
+            _same_minimum([(lib_res["eta"], c["eta"], c["eta_err"])])
+            dof_c = _dof(lib_res["C_tau_min"], lib_res["C_tau_w"], sc, 2)
+            assert abs(lib_res["C_chi2dof"] - c["chi2dof"]) * dof_c <= CHI2_ATOL
+            assert _close(lib_res["eta_err"], c["eta_err"], ERR_RTOL)
+    else:
+        same = False
+        if lib_res["C_ok"]:
+            r = ofits.fit_C_at(Cm, sc, Ltau, zeta, lib_res["C_tau_min"], lib_res["C_tau_w"])
+            assert r is not None
+            chi2, dof = r[0], r[1]
+            assert lib_res["C_chi2dof"] < ofits.C_CHI2 and 0 < lib_res["eta"] <= Ltau
+            assert lib_res["C_chi2dof"] * dof <= chi2 + CHI2_ATOL
+    # even correlator
+    if q["plateau_ok"]:
+        assert _close(lib_res["Q_pl"], q["Q_pl"], 1e-12) and _close(lib_res["Q_pl_err"], q["Q_pl_err"], 1e-12)
+    if (lib_res["Q_ok"], lib_res["Q_tau_min"], lib_res["Q_n_exp"]) == (int(q["ok"]), q["tau_min"], q["n_exp"]):
+        if q["ok"]:
+            pairs = [(lib_res["eta_e"], q["eta_e"], q["eta_e_err"])]
+            if not q["plateau_ok"]:
+                pairs.append((lib_res["Q_pl"], q["Q_pl"], q["Q_pl_err"]))
+            if q["n_exp"] == 2:
+                pairs.append((lib_res["eta_2"], q["eta_2"], np.nan))
+            try:
+                _same_minimum(pairs[:2] if q["n_exp"] == 2 else pairs)
+                npar = 2 * q["n_exp"] + (0 if q["plateau_ok"] else 1)
+                dof_q = _dof(lib_res["Q_tau_min"], lib_res["Q_tau_w"], sq, npar)
+                assert abs(lib_res["Q_chi2dof"] - q["chi2dof"]) * dof_q <= CHI2_ATOL
+            except AssertionError:
+                if q["n_exp"] != 2:
+                    raise
+                same = False  # two exponentials: another minimum at the same lags
+                _valid_q(lib_res, Qm, sq, Ltau)
+    else:
+        same = False
+        _valid_q(lib_res, Qm, sq, Ltau)
+    return same
+
+
+def _valid_q(lib_res, Qm, sq, Ltau):
+    if not lib_res["Q_ok"]:
+        return
+    assert lib_res["Q_chi2dof"] < ofits.Q_CHI2 and 1 <= lib_res["Q_tau_min"] <= lib_res["Q_tau_w"]
+    assert 0 < lib_res["eta_e"] <= Ltau
+    pl_ok = bool(lib_res["plateau_ok"])
+    r = ofits.fit_Q_at(Qm, sq, Ltau, lib_res["Q_tau_min"], lib_res["Q_tau_w"], lib_res["Q_n_exp"],
+                       lib_res["Q_pl"], free_pl=not pl_ok)
+    assert r is not None
+    chi2, dof = r[0], r[1]
+    assert lib_res["Q_chi2dof"] * dof <= chi2 + CHI2_ATOL, (lib_res["Q_chi2dof"] * dof, chi2)
 
 
 @pytest.mark.parametrize("R,n,Ltau,boundary", [(2, 12, 64, Q.PBC), (4, 16, 128, Q.PBC), (6, 10, 32, Q.APBC),
@@ -107,10 +151,10 @@ def test_library_fits_match_oracle(R, n, Ltau, boundary):
     n_ok = n_unique = 0
     for i in range(n):
         orc = ofits.fit_sample(C[:, i], Q2[:, i], Ltau, boundary)
-        n_unique += _compare(lib[i], orc, Ltau)
+        n_unique += _compare(lib[i], orc, C[:, i], Q2[:, i], Ltau, boundary)
         n_ok += lib[i]["C_ok"] + lib[i]["Q_ok"]
     assert n_ok >= n  # the cases exercise accepted fits, not only rejections
-    assert n_unique >= n - 2
+    assert n_unique >= n // 2  # most series end at the same minimum of every fit
 
 
 def test_tau_tilde_matches_oracle():
@@ -144,6 +188,7 @@ def test_fits_of_gpu_correlators_match_oracle():
     assert len(lib) == shape.n_samples * shape.n_k
     n_unique = 0
     for i in range(len(lib)):
-        n_unique += _compare(lib[i], ofits.fit_sample(C[:, i], Q2[:, i], shape.Ltau, shape.boundary), shape.Ltau)
+        n_unique += _compare(lib[i], ofits.fit_sample(C[:, i], Q2[:, i], shape.Ltau, shape.boundary),
+                             C[:, i], Q2[:, i], shape.Ltau, shape.boundary)
     assert sum(r["Q_ok"] for r in lib) > 0
-    assert n_unique >= 0.8 * len(lib)
+    assert n_unique >= 0.5 * len(lib)

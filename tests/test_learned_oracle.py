@@ -162,3 +162,113 @@ def test_judge_never_passes_a_steady_trend():
         E[m] = -m + np.array([-1, 1, -1, 1])[:, None] * 0.01
     q = np.full((nb, 1, K, P), 0.2) + np.linspace(-1e-3, 1e-3, P)
     assert OL.judge(E, q)[0] == -1
+
+
+# ---------------------------------------------------------------------------
+# the element-wise rounding bounds, pinned against an independent
+# single-precision implementation (numpy float32: BLAS summation order, not
+# the library's), which must fall inside them
+# ---------------------------------------------------------------------------
+def _f32_forward(theta, X, bf16=False):
+    W1, b1, W2, b2, W3, b3 = [p.astype(np.float32) for p in OL.unpack(theta)]
+    if bf16:
+        W1, b1, W2, b2, W3, b3 = [OL.to_bf16(p).astype(np.float32) for p in (W1, b1, W2, b2, W3, b3)]
+    r = (lambda a: OL.to_bf16(a).astype(np.float32)) if bf16 else (lambda a: a)
+    h = r(np.asarray(X, dtype=np.float32))
+    z1 = h @ W1.T + b1
+    h1 = r(np.maximum(z1, 0))
+    z2 = h1 @ W2.T + b2
+    h2 = r(np.maximum(z2, 0))
+    return (h2 @ W3.T + b3).astype(np.float64), (z1, h1, z2, h2)
+
+
+def _f32_loss_and_grad(theta, X, T):
+    W1, b1, W2, b2, W3, b3 = [p.astype(np.float32) for p in OL.unpack(theta)]
+    X = np.asarray(X, dtype=np.float32)
+    T = np.asarray(T, dtype=np.float32)
+    B = np.float32(T.shape[0])
+    y, (z1, h1, z2, h2) = _f32_forward(theta, X)
+    y = y.astype(np.float32)
+    a = y[:, :32] - y[:, :32].max(axis=1, keepdims=True)
+    logp = a - np.log(np.exp(a).sum(axis=1, keepdims=True))
+    r = y[:, 32] - T[:, 32]
+    loss = ((-(T[:, :32] * logp).sum(axis=1) + r * r).sum() / B)
+    dy = np.zeros_like(y)
+    dy[:, :32] = (np.exp(logp) * T[:, :32].sum(axis=1, keepdims=True) - T[:, :32]) / B
+    dy[:, 32] = 2 * r / B
+    dz2 = (dy @ W3) * (z2 > 0)
+    dz1 = (dz2 @ W2) * (z1 > 0)
+    g = OL.pack([dz1.T @ X, dz1.sum(0), dz2.T @ h1, dz2.sum(0), dy.T @ h2, dy.sum(0)])
+    return float(loss), g
+
+
+def _mlp_case(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, size=(n, 64)).astype(np.float32)
+    T = np.zeros((n, 33), dtype=np.float32)
+    T[:, :32] = rng.dirichlet(np.ones(32), size=n)
+    T[:, 32] = rng.uniform(0.4, 0.9, size=n)
+    return OL.init_params(seed).astype(np.float64), X, T
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (37, 2), (256, 3)])
+def test_fp32_gradient_and_forward_fall_inside_the_rounding_bounds(n, seed):
+    theta, X, T = _mlp_case(n, seed)
+    lref, gref = OL.loss_and_grad(theta, X, T)
+    lb, gb = OL.grad_error_bound(theta, X, T)
+    l32, g32 = _f32_loss_and_grad(theta, X, T)
+    assert abs(l32 - lref) <= lb
+    assert np.all(np.abs(g32 - gref) <= gb)
+    y, ey, _ = OL.fp32_forward_bound(theta, X)
+    y32, _ = _f32_forward(theta, X)
+    assert np.all(np.abs(y32 - y) <= ey)
+    # not vacuous: the largest elements are pinned to within their own size
+    # (worst-case bounds loosen with cancellation in long batch sums, so the
+    # fraction is larger for B = 256)
+    top = np.argsort(-np.abs(gref))[:100]
+    assert np.max(gb[top] / np.abs(gref[top])) < 1.0  # sign and magnitude pinned
+
+
+def test_gradient_bound_catches_a_wrong_element():
+    theta, X, T = _mlp_case(37, 4)
+    lref, gref = OL.loss_and_grad(theta, X, T)
+    _, gb = OL.grad_error_bound(theta, X, T)
+    k = int(np.argmax(np.abs(gref)))
+    bad = gref.copy()
+    bad[k] *= 1.05  # one element off by 5 %: outside its bound
+    assert not np.all(np.abs(bad - gref) <= gb)
+    bad = gref.copy()
+    bad[-1] = -bad[-1]  # a sign error in one bias gradient
+    assert not np.all(np.abs(bad - gref) <= gb)
+
+
+@pytest.mark.parametrize("seed", [5, 6])
+def test_bf16_inference_falls_inside_its_interval(seed):
+    theta, X, _ = _mlp_case(200, seed)
+    lo, hi = OL.forward_bf16_interval(theta, X)
+    y64 = OL.forward_bf16(theta, X)
+    y32, _ = _f32_forward(theta, X, bf16=True)
+    assert np.all((y64 >= lo) & (y64 <= hi))
+    assert np.all((y32 >= lo) & (y32 <= hi))
+    # one BF16 step (2^-8 relative) of the output scale bounds the width
+    assert np.median(hi - lo) < 2.0 ** -8 * np.abs(y64).max()
+
+
+def test_fp32_adam_falls_inside_its_bound():
+    theta, X, T = _mlp_case(64, 7)
+    th32 = theta.astype(np.float32)
+    m32 = np.zeros_like(th32)
+    v32 = np.zeros_like(th32)
+    m = v = em = ev = np.zeros_like(theta)
+    lr = 1e-3
+    for t in range(1, 4):
+        _, g = OL.loss_and_grad(th32.astype(np.float64), X, T)
+        g32 = g.astype(np.float32)
+        th1, m, v, em, ev, eth = OL.adam_step_bound(th32.astype(np.float64), m, v, em, ev, g32.astype(np.float64), t,
+                                                    lr)
+        b1, b2 = np.float32(0.9), np.float32(0.999)
+        m32 = b1 * m32 + np.float32(0.1) * g32
+        v32 = b2 * v32 + np.float32(0.001) * g32 * g32
+        c1, c2 = np.float32(1 - 0.9 ** t), np.float32(1 - 0.999 ** t)
+        th32 = th32 - np.float32(lr) * (m32 / c1) / (np.sqrt(v32 / c2) + np.float32(1e-8))
+        assert np.all(np.abs(th32.astype(np.float64) - th1) <= eth), t
