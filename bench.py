@@ -313,6 +313,13 @@ def run_ours(args, rank, world, local):
         # readback calls wait for their own copies)
         evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
         host = {"upload": 0.0, "step_enqueue": 0.0, "readback": 0.0}
+        # one untimed pass through the page-locked buffers first: the first
+        # device access to freshly pinned host pages sets up their mapping,
+        # a one-time cost of the buffers, not of a step
+        for gi, hs in enumerate(host_states):
+            ctx.qsg_set_spins(gi, hs.numpy().view(np.uint64))
+        for gi in range(len(w.shapes)):
+            ctx.qsg_read_correlators(gi, out=outs[gi])
         torch.cuda.synchronize()
         t_start = time.perf_counter()
         for i in range(args.steps):
@@ -336,15 +343,18 @@ def run_ours(args, rank, world, local):
         e2e_ms = (time.perf_counter() - t_start) * 1e3 / args.steps
         e2e_ms = max_over_ranks([e2e_ms], dist, "cuda")[0]
         dev = {"upload": 0.0, "step": 0.0, "readback": 0.0}
+        uploads = []
         for e in evs:
-            dev["upload"] += e[0].elapsed_time(e[1])
+            uploads.append(e[0].elapsed_time(e[1]))
+            dev["upload"] += uploads[-1]
             dev["step"] += e[1].elapsed_time(e[2])
             dev["readback"] += e[2].elapsed_time(e[3])
         e2e = {"value": whole_job_rate(updates_per_step, world, e2e_ms), "unit": "spin-flips/ns",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_ms,
                "breakdown_ms_per_step": {
                    "device_events": {k: v / args.steps for k, v in dev.items()},
-                   "host_wall": {k: 1e3 * v / args.steps for k, v in host.items()}}}
+                   "host_wall": {k: 1e3 * v / args.steps for k, v in host.items()},
+                   "upload_ms_each_step": uploads}}
 
     if rank != 0:
         if dist:
