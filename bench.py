@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-tune", action="store_true", help="keep the library's default launch options")
+    p.add_argument("--launch-options", default=None,
+                   help="fixed launch options instead of tuning, e.g. chunk=512,variant=0,persistent=1,graph=30,tail=28")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-ladder comparison")
     p.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
                    help="run one small untimed case for an ncu capture and exit")
@@ -54,9 +56,13 @@ def parse():
 # Small untimed cases for ncu captures (a few hundred MB to 2.4 GB on the
 # device, a handful of launches), named by what they exercise.
 def _case_sweep(Q, W):
-    # L=24, L_tau=2048, 128 samples, 1 replica, 32 k: 64 slots, 0.60 GB of state (> L2)
-    ctx = Q.Context([Q.Shape(24, 2048, 128, 1, 32, Q.HEATBATH, Q.PBC)])
+    # L=24, L_tau=2048, 128 samples, 2 replicas, 32 k: 128 slots, 1.21 GB of
+    # state (> L2), in the bench's launch form (512-plane chunks, the last 28
+    # slots in 128-plane chunks: 624 units, more than one wave of three blocks per SM)
+    ctx = Q.Context([Q.Shape(24, 2048, 128, 2, 32, Q.HEATBATH, Q.PBC)])
     ctx.qsg_init_samples(3, [W.uniform_ladder(0.22, 0.36, 32)])
+    ctx.qsg_set_option(Q.OPT_CHUNK, 512)
+    ctx.qsg_set_option(Q.OPT_TAIL, 28)
     ctx.qsg_sweep(4)
     return ctx
 
@@ -249,7 +255,15 @@ def run_ours(args, rank, world, local):
     # launch options (chunk, register variant, persistent launch, graph batch)
     # chosen by timing, before the warm-up; the sampled bits do not depend on them
     tuned = None
-    if not args.no_tune:
+    if args.launch_options:
+        from paper_2310_07486_gb300 import tuner
+        opts = dict(tuner.DEFAULTS)
+        for kv in args.launch_options.split(","):
+            k, v = kv.split("=")
+            opts[k.strip()] = int(v)
+        tuner.apply(ctx, opts)
+        tuned = {"options": opts}
+    elif not args.no_tune:
         from paper_2310_07486_gb300 import tuner
         tuned = tuner.tune(ctx, sweeps_per_call=sps)
 
