@@ -286,6 +286,17 @@ qsg_status qsg_read_accepts(qsg_ctx *ctx, int32_t group, int64_t *acc_host);
 qsg_status qsg_get_spins(qsg_ctx *ctx, int32_t group, uint64_t *host);
 qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host);
 
+/* The same state to or from a caller-owned DEVICE buffer of the same layout
+ * (slots x L_tau x L x L words, on the context's device), copied on the
+ * context's stream without waiting: ordered after the work enqueued before
+ * and before the work enqueued after.  A caller that stages the next state in
+ * device memory while the current one is being swept (an upload on another
+ * stream, synchronised with events) hides the host link behind the compute;
+ * the copy itself runs at device-memory speed.  set_spins_device also clears
+ * the cached actions.  A null buffer is QSG_ERR_ARG. */
+qsg_status qsg_get_spins_device(qsg_ctx *ctx, int32_t group, uint64_t *d_out);
+qsg_status qsg_set_spins_device(qsg_ctx *ctx, int32_t group, const uint64_t *d_words);
+
 /* Counters: sweeps done, tempering steps done, measurements accumulated.
  * The sweep and swap counters key the Philox streams, so restoring them with
  * the spins (and the couplings, re-drawn by qsg_init_samples from the same

@@ -692,6 +692,23 @@ qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host) {
     return QSG_OK;
 }
 
+qsg_status qsg_get_spins_device(qsg_ctx *ctx, int32_t group, uint64_t *d_out) {
+    if (!ctx || !d_out || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, cudaMemcpyAsync(d_out, g.S, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    return QSG_OK;
+}
+
+qsg_status qsg_set_spins_device(qsg_ctx *ctx, int32_t group, const uint64_t *d_words) {
+    if (!ctx || !d_words || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, cudaMemcpyAsync(g.S, d_words, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    ctx->energy_fresh = false;
+    return QSG_OK;
+}
+
 qsg_status qsg_get_counters(qsg_ctx *ctx, uint32_t *sweeps, uint32_t *swaps, int64_t *n_meas) {
     if (!ctx) return QSG_ERR_ARG;
     if (sweeps) *sweeps = ctx->sweeps;

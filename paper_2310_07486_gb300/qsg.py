@@ -111,6 +111,10 @@ def load_library(path: str | None = None):
     lib.qsg_get_spins.argtypes = [vp, i32, vp]
     lib.qsg_set_spins.restype = i32
     lib.qsg_set_spins.argtypes = [vp, i32, vp]
+    lib.qsg_get_spins_device.restype = i32
+    lib.qsg_get_spins_device.argtypes = [vp, i32, vp]
+    lib.qsg_set_spins_device.restype = i32
+    lib.qsg_set_spins_device.argtypes = [vp, i32, vp]
     lib.qsg_get_counters.restype = i32
     lib.qsg_get_counters.argtypes = [vp, vp, vp, vp]
     lib.qsg_set_counters.restype = i32
@@ -133,6 +137,7 @@ def exported_symbols():
     return ["qsg_workspace_bytes", "qsg_create", "qsg_destroy", "qsg_set_stream", "qsg_init_samples",
             "qsg_set_couplings", "qsg_sweep", "qsg_tempering_swap", "qsg_measure_correlators",
             "qsg_read_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
+            "qsg_get_spins_device", "qsg_set_spins_device",
             "qsg_get_counters", "qsg_set_counters", "qsg_set_option", "qsg_sweep_static_scratch", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
 
 
@@ -364,6 +369,27 @@ class Context:
     def qsg_set_spins(self, group, words):
         words = np.ascontiguousarray(words, dtype=np.uint64)
         self._check(self.lib.qsg_set_spins(self.h, group, _ptr(words)), "qsg_set_spins")
+
+    def _check_device_words(self, group, t, what):
+        import torch
+        s = self.shapes[group]
+        n = s.slots * s.Ltau * s.L * s.L
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int64 and t.is_contiguous()
+                and t.numel() == n and t.device == self.device):
+            raise QSGError(-1, what, "need a contiguous int64 tensor of %d words on %s" % (n, self.device))
+
+    def qsg_get_spins_device(self, group, out):
+        """Spin words into a device tensor (int64, the layout of qsg_get_spins),
+        ordered on the context's stream, no host wait."""
+        self._check_device_words(group, out, "qsg_get_spins_device")
+        self._check(self.lib.qsg_get_spins_device(self.h, group, ctypes.c_void_p(out.data_ptr())),
+                    "qsg_get_spins_device")
+
+    def qsg_set_spins_device(self, group, words):
+        """Spin words from a device tensor, ordered on the context's stream."""
+        self._check_device_words(group, words, "qsg_set_spins_device")
+        self._check(self.lib.qsg_set_spins_device(self.h, group, ctypes.c_void_p(words.data_ptr())),
+                    "qsg_set_spins_device")
 
     def qsg_get_counters(self):
         a, b, c = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_int64()

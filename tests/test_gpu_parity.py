@@ -542,3 +542,31 @@ def test_unit_kernel_chunks_and_tails_match_oracle(L, algo, boundary, Ltau, chun
         assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
     finally:
         ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, 0)
+
+
+def test_device_buffer_checkpoint_resume_is_bit_exact():
+    """qsg_get_spins_device / qsg_set_spins_device: the state through a device
+    buffer equals the host copy, and resuming from it repeats the run bit for
+    bit (the copies are ordered on the context's stream)."""
+    shape = Q.Shape(24, 64, 70, 2, 3, Q.HEATBATH, Q.APBC)
+    lad = np.array([0.25, 0.3, 0.35])
+    ctx = Q.Context([shape])
+    ctx.qsg_init_samples(12, [lad])
+    ctx.qsg_sweep(3)
+    ctx.qsg_tempering_swap()
+    n = shape.slots * shape.Ltau * shape.L * shape.L
+    saved = torch.empty(n, dtype=torch.int64, device=ctx.device)
+    ctx.qsg_get_spins_device(0, saved)
+    counters = ctx.qsg_get_counters()
+    host = ctx.qsg_get_spins(0)
+    assert np.array_equal(saved.cpu().numpy().view(np.uint64).reshape(host.shape), host)
+    ctx.qsg_sweep(4)
+    ctx.qsg_tempering_swap()
+    first = ctx.qsg_get_spins(0)
+    ctx.qsg_set_spins_device(0, saved)  # no host wait: ordered before the sweeps below
+    ctx.qsg_set_counters(*counters)
+    ctx.qsg_sweep(4)
+    ctx.qsg_tempering_swap()
+    assert np.array_equal(ctx.qsg_get_spins(0), first)
+    with pytest.raises(Q.QSGError):
+        ctx.qsg_set_spins_device(0, saved[:-1])
