@@ -150,6 +150,13 @@ double levmar(const Model &m, const Data &d, double *p, double *err) {
         }
     };
     normal(p);
+    // up to three passes: a pass that ends on a tiny step or a flat chi2 after
+    // the damping has grown large may stop short in a long curved valley (the
+    // two-exponential fits); a restart with the damping reset either moves
+    // on or confirms the end point
+    for (int pass = 0; pass < 3; ++pass) {
+    const double chi2_start = chi2;
+    lambda = 1e-3;
     for (int it = 0; it < 2000 && lambda < 1e30; ++it) {
         double M[kMaxPar][kMaxPar], step[kMaxPar], trial[kMaxPar];
         for (int a = 0; a < np; ++a) {
@@ -176,6 +183,8 @@ double levmar(const Model &m, const Data &d, double *p, double *err) {
         lambda = std::fmax(lambda * 0.1, 1e-15);
         normal(p);
         if (small || flat) break;
+    }
+    if (!(chi2 < chi2_start * (1.0 - 1e-12))) break;
     }
     // errors: sqrt of the diagonal of (J^T W J)^-1, column by column
     for (int a = 0; a < np; ++a) {
