@@ -48,6 +48,7 @@ def parse():
     p.add_argument("--launch-options", default=None,
                    help="fixed launch options instead of tuning, e.g. chunk=512,variant=0,persistent=1,graph=30,tail=28")
     p.add_argument("--no-learned", action="store_true", help="skip the learned-ladder comparison")
+    p.add_argument("--no-ragged", action="store_true", help="skip the ragged multi-group sweep timing")
     p.add_argument("--profile-case", choices=sorted(PROFILE_CASES),
                    help="run one small untimed case for an ncu capture and exit")
     return p.parse_args()
@@ -320,7 +321,7 @@ def run_ours(args, rank, world, local):
         h2d = 0
         for gi, s in enumerate(w.shapes):
             words = ctx.qsg_get_spins(gi)
-            pinned = torch.from_numpy(words.view(np.int64)).pin_memory()
+            pinned = torch.from_numpy(words.reshape(-1).view(np.int64)).pin_memory()
             host_states.append(pinned)
             h2d += words.nbytes
         d2h = sum(2 * s.n_replicas * s.n_samples * s.n_k * s.n_lag * 8 + s.n_samples * s.n_k * 8 for s in w.shapes)
@@ -416,6 +417,8 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
         "e2e": e2e,
     }
+    if world == 1 and not args.no_ragged:
+        out["ragged"] = ragged_sweeps(load_peaks()[0]["hbm_gbs"])
     if world == 1 and not args.no_learned:
         out["learned_ladder"] = learned_ladder()
     if world == 1 and not args.no_cpu_baseline:
@@ -425,16 +428,54 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def ragged_sweeps(peak_gbs, reps=4, batch=30):
+    """The ragged workload (640 samples in five groups, L = 8 .. 24, L_tau =
+    128 .. 2048, 6.47 GB of state): sweeps of every group, device-timed with
+    CUDA events in each way of launching several groups (30-sweep CUDA
+    graphs): one launch per group in order, one persistent launch, one stream
+    per group."""
+    import torch
+
+    from paper_2310_07486_gb300 import qsg as Q
+    from paper_2310_07486_gb300 import workloads
+    w = workloads.ragged()
+    ctx = Q.Context(w.shapes)
+    ctx.qsg_init_samples(w.seed, w.ladders)
+    ctx.qsg_set_option(Q.OPT_GRAPH, batch)
+    st = ctx.stream
+    ms = {}
+    for name, mode in (("sequential", 1), ("persistent", 2), ("concurrent", 3)):
+        ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
+        ctx.qsg_sweep(batch)  # capture and warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            ctx.qsg_sweep(batch)
+        b.record(st)
+        b.synchronize()
+        ms[name] = a.elapsed_time(b) / (reps * batch)
+    best = min(ms, key=ms.get)
+    gbs = 16 * w.words / (ms[best] * 1e-3) / 1e9
+    ctx.close()
+    return {"workload": w.name, "state_bytes": 8 * w.words, "ms_per_sweep": ms, "best": best,
+            "spin_flips_per_ns": w.spin_updates_per_sweep / (ms[best] * 1e6),
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs}}
+
+
 def learned_ladder():
-    """GPU-seconds per sample to pass the log-binning judge with the learned
-    ladders against the uniform ladder (scaled-down study: training runs at
-    L = 4, 6, evaluation on 256 fresh samples at L = 8, L_tau = 32)."""
+    """GPU-seconds per thermalised sample (the log-binning judge, runs capped
+    at 2^14 sweeps) with the learned ladders against the uniform ladder
+    (scaled-down study: training runs at L = 6, 8, 10, evaluation on 256
+    fresh samples at L = 12, L_tau = 64; one seed here, with the paired
+    bootstrap interval over its samples)."""
     from paper_2310_07486_gb300 import ladder, workloads
+    st = workloads.ladder_study()
     try:
-        out = ladder.study_main(workloads.ladder_study(), log=lambda *a: None)
+        out = ladder.study_main(st, seeds=[st.seeds[0]], log=lambda *a: None)
     except Exception as e:  # reported, not fatal for the throughput line
         return {"error": repr(e)}
-    out["metric"] = "GPU-s/sample to pass the judge, learned vs plain ladder"
+    out.pop("per_seed", None)
     return out
 
 

@@ -322,11 +322,18 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *   QSG_OPT_CORR_KERNEL   0 = tensor cores (Gram tiles by tcgen05.mma in FP8,
  *                         exact for +-1 spins), 1 = XOR/popcount on the
  *                         integer pipes
- *   QSG_OPT_PERSISTENT    0 = automatic (on when the context has several
- *                         groups), 1 = off (one launch per group and sweep),
- *                         2 = on: one persistent launch per sweep serves every
- *                         group from a work queue, largest groups first (needs
- *                         one algorithm, L <= 24, every L_tau % 16 == 0)
+ *   QSG_OPT_PERSISTENT    how the groups of a context are swept:
+ *                         0 = automatic (mode 3 when the context has several
+ *                         groups), 1 = one launch per group and sweep, in
+ *                         group order on the context's stream, 2 = one
+ *                         persistent launch per sweep serves every group from
+ *                         a work queue, largest groups first (needs one
+ *                         algorithm, L <= 24, every L_tau % 16 == 0), 3 = each
+ *                         group's sweeps on a stream of its own, forked from
+ *                         and joined back into the context's stream (inside
+ *                         the CUDA graph when QSG_OPT_GRAPH is on), so that
+ *                         the groups' launches overlap and small groups fill
+ *                         the last waves of large ones
  *   QSG_OPT_GRAPH         0 = off; G in 1..4096 = qsg_sweep replays a CUDA
  *                         graph of G sweeps (captured on first use and again
  *                         after an option change) for each whole batch of G,

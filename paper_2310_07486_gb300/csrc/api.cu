@@ -205,7 +205,7 @@ struct qsg_ctx {
     int sweep_kernel = 0;  // QSG_OPT_SWEEP_KERNEL
     int chunk = 0;         // QSG_OPT_CHUNK
     int corr_tensor = 1;   // QSG_OPT_CORR_KERNEL: 1 tensor cores, 0 integer pipes
-    int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 on
+    int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 persistent kernel, 3 one stream per group
     int triples = 1;       // QSG_OPT_ONETIME: 1 with the three-replica sums, 0 without
     int tail = 0;          // QSG_OPT_TAIL: slots swept in quarter-length chunks, last
     unsigned wait_limit = kDefaultWaitLimit;  // QSG_OPT_WAIT_LIMIT: polls per bounded device wait
@@ -222,9 +222,17 @@ struct qsg_ctx {
     unsigned long long graph_launches = 0;  // kernels per replay
     bool base_valid = false;
     std::string last_cuda;
+    // one stream per group for the concurrent multi-group mode, with the fork
+    // and join events that order them against the context's stream
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> joins;
+    cudaEvent_t fork = nullptr;
     ~qsg_ctx() {
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (cudaStream_t t : side) cudaStreamDestroy(t);
+        for (cudaEvent_t e : joins) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
     }
 };
 
@@ -421,6 +429,61 @@ qsg_status qsg_set_couplings(qsg_ctx *ctx, int32_t group, const int8_t *J_host) 
 }
 
 // Launch one sweep of every group; the sweep index is *sb + idx (sb may be null).
+// How the groups of one sweep are launched.
+enum SweepMode { MODE_SEQUENTIAL = 0, MODE_PERSISTENT = 1, MODE_CONCURRENT = 2 };
+
+static SweepMode sweep_mode(const qsg_ctx *ctx) {
+    if (ctx->sweep_kernel == 1 || ctx->groups.size() < 2) return MODE_SEQUENTIAL;
+    if (ctx->persistent == 2 && ctx->plan_ok) return MODE_PERSISTENT;
+    if (ctx->persistent == 1) return MODE_SEQUENTIAL;
+    return MODE_CONCURRENT;  // 3, or automatic with several groups
+}
+
+static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t *sb, uint32_t idx, cudaStream_t st);
+
+// `count` sweeps of every group with indices first .. first + count - 1 (added
+// to *sb when sb is given).  Concurrent mode: each group's chain of sweeps on
+// its own stream, forked from st and joined back into it (groups share no
+// data, so only each group's own sweeps are ordered).
+static qsg_status launch_sweeps(qsg_ctx *ctx, SweepMode mode, const uint32_t *sb, uint32_t first, int count,
+                                cudaStream_t st) {
+    if (mode != MODE_CONCURRENT) {
+        for (int i = 0; i < count; ++i) {
+            qsg_status s = launch_one_sweep(ctx, mode == MODE_PERSISTENT, sb, first + (uint32_t)i, st);
+            if (s != QSG_OK) return s;
+        }
+        return QSG_OK;
+    }
+    const size_t ng = ctx->groups.size();
+    if (!ctx->fork) QSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+    while (ctx->side.size() < ng) {
+        cudaStream_t t = nullptr;
+        cudaEvent_t e = nullptr;
+        QSG_CUDA(ctx, cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        ctx->side.push_back(t);
+        QSG_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->joins.push_back(e);
+    }
+    QSG_CUDA(ctx, cudaEventRecord(ctx->fork, st));
+    for (size_t gi = 0; gi < ng; ++gi) {
+        const Group &g = ctx->groups[gi];
+        cudaStream_t t = ctx->side[gi];
+        QSG_CUDA(ctx, cudaStreamWaitEvent(t, ctx->fork, 0));
+        const int C = wavefront_chunk(g, ctx->chunk);
+        for (int i = 0; i < count; ++i) {
+            if (C > 0)
+                QSG_CUDA(ctx, launch_sweep_wavefront(g, sb, first + (uint32_t)i, ctx->seed, g.arrivals, C, ctx->tail, t));
+            else if (sb)
+                return QSG_ERR_ARG;
+            else
+                QSG_CUDA(ctx, launch_sweep_reference(g, first + (uint32_t)i, ctx->seed, t));
+        }
+        QSG_CUDA(ctx, cudaEventRecord(ctx->joins[gi], t));
+        QSG_CUDA(ctx, cudaStreamWaitEvent(st, ctx->joins[gi], 0));
+    }
+    return QSG_OK;
+}
+
 static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t *sb, uint32_t idx, cudaStream_t st) {
     if (persistent) {
         QSG_CUDA(ctx, launch_sweep_persistent(ctx->plan, sb, idx, ctx->seed, st));
@@ -439,8 +502,8 @@ static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t
 }
 
 // (Re)capture the graph of graph_batch sweeps when a launch option changed.
-static qsg_status ensure_graph(qsg_ctx *ctx, bool persistent) {
-    const long long key = (((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 2 + (persistent ? 1 : 0)) * 2 +
+static qsg_status ensure_graph(qsg_ctx *ctx, SweepMode mode) {
+    const long long key = (((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 4 + (int)mode) * 4 +
                             g_wavefront_variant) * 65537LL + ctx->chunk) * 65537LL + ctx->tail;
     if (ctx->graph_exec && ctx->graph_key == key) return QSG_OK;
     if (ctx->graph_exec) {
@@ -450,9 +513,7 @@ static qsg_status ensure_graph(qsg_ctx *ctx, bool persistent) {
     if (!ctx->cap_stream) QSG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
     const unsigned long long before = g_launches.load();
     QSG_CUDA(ctx, cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeRelaxed));
-    qsg_status s = QSG_OK;
-    for (int i = 0; i < ctx->graph_batch && s == QSG_OK; ++i)
-        s = launch_one_sweep(ctx, persistent, ctx->pb.sweep_base, (uint32_t)i, ctx->cap_stream);
+    qsg_status s = launch_sweeps(ctx, mode, ctx->pb.sweep_base, 0u, ctx->graph_batch, ctx->cap_stream);
     if (s == QSG_OK && launch_add_word(ctx->pb.sweep_base, (uint32_t)ctx->graph_batch, ctx->cap_stream) != cudaSuccess)
         s = QSG_ERR_CUDA;
     cudaGraph_t graph = nullptr;
@@ -480,12 +541,11 @@ qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
     if (!ctx || n_sweeps < 0) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
     if ((uint64_t)ctx->sweeps + (uint64_t)n_sweeps > 0xFFFFFFFFull) return QSG_ERR_ARG;
-    const bool persistent = ctx->plan_ok && ctx->sweep_kernel != 1 &&
-                            (ctx->persistent == 2 || (ctx->persistent == 0 && ctx->groups.size() > 1));
+    const SweepMode mode = sweep_mode(ctx);
     int done = 0;
     const int G = ctx->graph_batch;
     if (G > 0 && n_sweeps >= G) {
-        qsg_status s = ensure_graph(ctx, persistent);
+        qsg_status s = ensure_graph(ctx, mode);
         if (s != QSG_OK) return s;
         if (!ctx->base_valid) {
             QSG_CUDA(ctx, launch_set_word(ctx->pb.sweep_base, ctx->sweeps, ctx->stream));
@@ -497,10 +557,10 @@ qsg_status qsg_sweep(qsg_ctx *ctx, int32_t n_sweeps) {
             ctx->sweeps += (uint32_t)G;
         }
     }
-    for (; done < n_sweeps; ++done) {
-        qsg_status s = launch_one_sweep(ctx, persistent, nullptr, ctx->sweeps, ctx->stream);
+    if (done < n_sweeps) {
+        qsg_status s = launch_sweeps(ctx, mode, nullptr, ctx->sweeps, n_sweeps - done, ctx->stream);
         if (s != QSG_OK) return s;
-        ctx->sweeps++;
+        ctx->sweeps += (uint32_t)(n_sweeps - done);
         ctx->base_valid = false;
     }
     if (n_sweeps > 0) ctx->energy_fresh = false;
@@ -744,7 +804,7 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
         return QSG_OK;
     }
     if (option == QSG_OPT_PERSISTENT) {
-        if (value < 0 || value > 2) return QSG_ERR_ARG;
+        if (value < 0 || value > 3) return QSG_ERR_ARG;
         if (value == 2 && !ctx->plan_ok) return QSG_ERR_ARG;
         ctx->persistent = (int)value;
         return QSG_OK;

@@ -151,13 +151,20 @@ def ladder_targets(sigma_E, ladder, k_min, k_max, fine=4096):
     return out
 
 
+SIZE_FEATURE = 63  # model input replaced by the lattice size (the coupling feature at offset (0, 8))
+
+
 def features_of(J, L, Ltau):
-    """The 64 coupling features of every sample (computed on the GPU)."""
+    """Model inputs of every sample: the 64 coupling features (computed on the
+    GPU), with input SIZE_FEATURE replaced by log2(L^2 L_tau) / 16 so that one
+    predictor serves several lattice sizes (the sweep budget grows steeply
+    with the size, which the coupling statistics alone do not carry)."""
     ctx = Q.Context([Q.Shape(L, Ltau, len(J), 1, 1)])
     ctx.qsg_init_samples(1, [np.array([0.3])])
     ctx.qsg_set_couplings(0, J)
     X = ctx.qsg_sample_features(0)
     ctx.close()
+    X[:, SIZE_FEATURE] = math.log2(L * L * Ltau) / 16.0
     return X
 
 
@@ -248,13 +255,55 @@ def compare(study, mlp, log=print):
     out["gain"] = out["plain"]["gpu_s_per_sample"] / max(out["learned"]["gpu_s_per_sample"], 1e-30)
     log(f"  plain:   passed {out['plain']['passed']:.2f}, mean sweeps {out['plain']['mean_sweeps']:.0f}")
     log(f"  learned: passed {out['learned']['passed']:.2f}, mean sweeps {out['learned']['mean_sweeps']:.0f}")
+    # per-sample costs in the plain arm's sample order, for paired statistics
+    out["_per_sample"] = {"plain": plain.gpu_seconds_per_sample(), "learned": learned.gpu_seconds_per_sample()[inv],
+                          "plain_passed": plain.first_pass_bin >= 0,
+                          "learned_passed": learned.first_pass_bin[inv] >= 0,
+                          "pred_log2_budget": 16.0 * Y[:, 32].astype(np.float64),
+                          "log2_sweeps_plain": np.log2(plain.sweeps_to_pass)}
     return out
 
 
-def study_main(study=None, log=print):
-    """The whole learned-ladder study: training runs, training, comparison."""
+def per_passed(cost, passed):
+    """GPU-seconds spent on the samples (each until it passed, or to the cap)
+    per sample that passed the judge: the cost of one thermalised sample when
+    the runs are capped (the mean of the capped costs when every sample
+    passes)."""
+    n = np.sum(passed, axis=-1)
+    return np.sum(cost, axis=-1) / np.maximum(n, 1) + np.where(n > 0, 0.0, np.inf)
+
+
+def paired_bootstrap(plain, learned, plain_passed=None, learned_passed=None, n_boot=4000, seed=0, level=0.95):
+    """Gain of the learned ladders (plain cost over learned cost) and its
+    percentile interval from resampling the samples, both arms together so
+    that each sample keeps its own pair of outcomes.  Without pass flags the
+    cost is the mean GPU-seconds per sample (capped); with them, the
+    GPU-seconds per sample that passed (per_passed)."""
+    plain = np.asarray(plain, dtype=np.float64)
+    learned = np.asarray(learned, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    idx = rng.integers(0, len(plain), size=(n_boot, len(plain)))
+    if plain_passed is None:
+        ratios = plain[idx].mean(axis=1) / learned[idx].mean(axis=1)
+        point = plain.mean() / learned.mean()
+    else:
+        pp = np.asarray(plain_passed, dtype=bool)
+        lp = np.asarray(learned_passed, dtype=bool)
+        ratios = per_passed(plain[idx], pp[idx]) / per_passed(learned[idx], lp[idx])
+        point = per_passed(plain, pp) / per_passed(learned, lp)
+    lo, hi = np.quantile(ratios, [(1 - level) / 2, (1 + level) / 2])
+    return float(point), float(lo), float(hi)
+
+
+def _rank(a):
+    r = np.empty(len(a))
+    r[np.argsort(a, kind="stable")] = np.arange(len(a))
+    return r
+
+
+def study_one(study, log=print):
+    """One seed of the study: training runs, training, comparison."""
     import time
-    study = study or W.ladder_study()
     t0 = time.time()
     X, T = training_set(study, log)
     t1 = time.time()
@@ -262,9 +311,76 @@ def study_main(study=None, log=print):
     t2 = time.time()
     log(f"  trained on {len(X)} samples: loss {losses[:10].mean():.4f} -> {losses[-10:].mean():.4f}")
     out = compare(study, mlp, log)
+    # the budget head across the training sizes: predicted against actual
+    # mean log2 sweeps per size
+    sizes = []
+    n = study.n_train_per_size
+    Yt = mlp.predict(X, bf16=True)
+    for si, (L, Lt) in enumerate(study.train_sizes):
+        sl = slice(si * n, (si + 1) * n)
+        sizes.append({"L": L, "Ltau": Lt, "pred_mean_log2_budget": float(16.0 * Yt[sl, 32].mean()),
+                      "actual_mean_log2_sweeps": float(16.0 * T[sl, 32].mean())})
+    out["budget_by_training_size"] = sizes
     out["train_samples"] = int(len(X))
     out["train_loss_first_last"] = [float(losses[:10].mean()), float(losses[-10:].mean())]
     out["wall_s"] = {"training_runs": t1 - t0, "training": t2 - t1, "comparison": time.time() - t2}
+    return out
+
+
+def study_main(study=None, seeds=None, log=print):
+    """The learned-ladder study over several seeds (training samples,
+    predictor initialisation and evaluation samples all change with the
+    seed): per seed, the gain in GPU-seconds per sample; pooled over every
+    evaluation sample, the gain with a paired bootstrap interval; and how the
+    budget head's predictions track the sweeps the judge needed."""
+    from dataclasses import replace
+    study = study or W.ladder_study()
+    seeds = list(seeds) if seeds is not None else list(study.seeds)
+    per_seed, plain_c, learned_c, plain_p, learned_p, pred, actual = [], [], [], [], [], [], []
+    for sd in seeds:
+        log(f" seed {sd}")
+        o = study_one(replace(study, seed=sd), log)
+        ps = o.pop("_per_sample")
+        plain_c.append(ps["plain"])
+        learned_c.append(ps["learned"])
+        plain_p.append(ps["plain_passed"])
+        learned_p.append(ps["learned_passed"])
+        pred.append(ps["pred_log2_budget"])
+        actual.append(ps["log2_sweeps_plain"])
+        o["gain_per_passed_sample"] = float(per_passed(ps["plain"], ps["plain_passed"])
+                                            / per_passed(ps["learned"], ps["learned_passed"]))
+        per_seed.append(o)
+    plain_c, learned_c = np.concatenate(plain_c), np.concatenate(learned_c)
+    plain_p, learned_p = np.concatenate(plain_p), np.concatenate(learned_p)
+    pred, actual = np.concatenate(pred), np.concatenate(actual)
+    gain, lo, hi = paired_bootstrap(plain_c, learned_c, plain_p, learned_p)
+    gain_m, lo_m, hi_m = paired_bootstrap(plain_c, learned_c)
+    L, Lt = study.eval_size
+    out = {
+        "metric": "GPU-s/sample to pass the judge, learned vs plain ladder",
+        "eval_size": {"L": L, "Ltau": Lt, "samples_per_seed": study.n_eval, "k": [study.k_min, study.k_max],
+                      "n_k": study.n_k, "replicas": study.replicas, "cap_sweeps": 2 ** study.max_bin},
+        "train_sizes": [list(x) for x in study.train_sizes], "train_samples_per_size": study.n_train_per_size,
+        "seeds": seeds,
+        "gain": gain, "gain_interval95": [lo, hi],
+        "gain_is": "plain over learned GPU-seconds per sample that passed the judge (the samples' costs until "
+                   "they passed or hit the cap, summed, per passing sample)",
+        "interval": "paired bootstrap over the pooled evaluation samples",
+        "gain_per_seed": [o["gain_per_passed_sample"] for o in per_seed],
+        "gain_capped_mean": gain_m, "gain_capped_mean_interval95": [lo_m, hi_m],
+        "plain_gpu_s_per_passed_sample": float(per_passed(plain_c, plain_p)),
+        "learned_gpu_s_per_passed_sample": float(per_passed(learned_c, learned_p)),
+        "plain_gpu_s_per_sample_capped": float(plain_c.mean()),
+        "learned_gpu_s_per_sample_capped": float(learned_c.mean()),
+        "plain_passed": float(np.mean([o["plain"]["passed"] for o in per_seed])),
+        "learned_passed": float(np.mean([o["learned"]["passed"] for o in per_seed])),
+        "budget_within_eval_size": {
+            "pearson": float(np.corrcoef(pred, actual)[0, 1]) if actual.std() > 0 else None,
+            "spearman": float(np.corrcoef(_rank(pred), _rank(actual))[0, 1]) if actual.std() > 0 else None,
+            "pred_mean_log2": float(pred.mean()), "actual_mean_log2": float(actual.mean())},
+        "budget_by_training_size": per_seed[0]["budget_by_training_size"],
+        "per_seed": per_seed,
+    }
     return out
 
 
@@ -276,6 +392,7 @@ if __name__ == "__main__":
     ap.add_argument("--train-per-size", type=int, default=None)
     ap.add_argument("--eval", type=int, default=None)
     ap.add_argument("--max-bin", type=int, default=None)
+    ap.add_argument("--seeds", type=int, default=None, help="number of seeds (default: the study's)")
     a = ap.parse_args()
     st = W.ladder_study()
     if a.train_per_size:
@@ -284,4 +401,5 @@ if __name__ == "__main__":
         st.n_eval = a.eval
     if a.max_bin:
         st.max_bin = a.max_bin
-    print(json.dumps(study_main(st)), flush=True)
+    seeds = list(st.seeds)[:a.seeds] if a.seeds else None
+    print(json.dumps(study_main(st, seeds=seeds)), flush=True)

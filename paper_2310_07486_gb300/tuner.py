@@ -61,7 +61,7 @@ def candidate_chunks(shapes, largest=512):
 
 def candidates(shapes, sweeps_per_call):
     chunks = candidate_chunks(shapes)
-    persistent = [1, 2] if len(shapes) > 1 else [1]
+    persistent = [1, 2, 3] if len(shapes) > 1 else [1]
     graph = [0, sweeps_per_call] if sweeps_per_call > 1 else [0]
     for chunk, variant, pers, gr in itertools.product(chunks, VARIANTS, persistent, graph):
         yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0}

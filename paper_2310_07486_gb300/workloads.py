@@ -87,10 +87,12 @@ def bimodal_couplings(n: int, L: int, seed: int) -> np.ndarray:
 @dataclass
 class LadderStudy:
     """Sizes of the learned-ladder study (scaled down from 2000 training runs
-    at L = 12..20 and 256 evaluation samples at L = 24, L_tau = 2048)."""
-    train_sizes: list = field(default_factory=lambda: [(4, 16), (6, 32)])
-    n_train_per_size: int = 1024
-    eval_size: tuple = (8, 32)
+    at L = 12..20 and 256 evaluation samples at L = 24, L_tau = 2048):
+    training runs at three sizes, evaluation on fresh samples at a larger
+    one, a judge capped at 2^max_bin sweeps, several seeds."""
+    train_sizes: list = field(default_factory=lambda: [(6, 32), (8, 48), (10, 64)])
+    n_train_per_size: int = 640
+    eval_size: tuple = (12, 64)
     n_eval: int = 256
     k_min: float = 0.2
     k_max: float = 0.45
@@ -99,6 +101,7 @@ class LadderStudy:
     sweeps_per_swap: int = 8
     max_bin: int = 14          # bins of sweeps (2^m, 2^(m+1)], m < max_bin
     seed: int = 2024
+    seeds: tuple = (2024, 2025, 2026)
 
 
 def ladder_study() -> LadderStudy:

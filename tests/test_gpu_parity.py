@@ -306,13 +306,16 @@ def test_correlator_kernels_match_oracle(L, Ltau, boundary):
 
 @pytest.mark.parametrize("algo", [Q.METROPOLIS, Q.HEATBATH])
 def test_persistent_ragged_launch_matches_oracle(algo):
-    """Groups of different (L, L_tau) in one persistent launch per sweep: every
-    group's spins equal the oracle's and the per-group launches'."""
+    """Groups of different (L, L_tau) in one persistent launch per sweep, and
+    on one stream each: every group's spins equal the oracle's and the
+    sequential per-group launches'."""
     shapes = [Q.Shape(8, 32, 70, 2, 3, algo, Q.PBC), Q.Shape(12, 64, 5, 1, 2, algo, Q.APBC),
-              Q.Shape(6, 16, 64, 2, 2, algo, Q.PBC), Q.Shape(16, 48, 3, 1, 1, algo, Q.PBC)]
-    lads = [np.array([0.2, 0.3, 0.4]), np.array([0.25, 0.33]), np.array([0.27, 0.28]), np.array([0.3])]
+              Q.Shape(6, 16, 64, 2, 2, algo, Q.PBC), Q.Shape(16, 48, 3, 1, 1, algo, Q.PBC),
+              Q.Shape(24, 32, 66, 1, 2, algo, Q.APBC)]
+    lads = [np.array([0.2, 0.3, 0.4]), np.array([0.25, 0.33]), np.array([0.27, 0.28]), np.array([0.3]),
+            np.array([0.26, 0.31])]
     results = []
-    for mode in (2, 1):  # persistent on, off
+    for mode in (2, 1, 3):  # persistent kernel, sequential, one stream per group
         ctx = Q.Context(shapes)
         ctx.qsg_init_samples(23, lads)
         ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
@@ -320,8 +323,9 @@ def test_persistent_ragged_launch_matches_oracle(algo):
             ctx.qsg_sweep(2)
             ctx.qsg_tempering_swap()
         results.append([ctx.qsg_get_spins(gi) for gi in range(len(shapes))])
-    for a, b in zip(*results):
-        assert np.array_equal(a, b)
+    for other in results[1:]:
+        for a, b in zip(results[0], other):
+            assert np.array_equal(a, b)
     for gid, (s, l) in enumerate(zip(shapes, lads)):
         o = oracle.OracleGroup(s.L, s.Ltau, s.n_samples, s.n_replicas, s.n_k, algo=s.algo, boundary=s.boundary,
                                group_id=gid)
@@ -335,7 +339,7 @@ def test_persistent_ragged_launch_matches_oracle(algo):
 def test_ragged_workload_persistent_equals_per_group():
     w = workloads.ragged()
     out = []
-    for mode in (2, 1):
+    for mode in (2, 1, 3):
         ctx = Q.Context(w.shapes)
         ctx.qsg_init_samples(w.seed, w.ladders)
         ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
@@ -343,11 +347,12 @@ def test_ragged_workload_persistent_equals_per_group():
         out.append([ctx.qsg_get_spins(gi) for gi in range(len(w.shapes))])
         del ctx
         torch.cuda.empty_cache()
-    for a, b in zip(*out):
-        assert np.array_equal(a, b)
+    for other in out[1:]:
+        for a, b in zip(out[0], other):
+            assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("persistent", [1, 2])
+@pytest.mark.parametrize("persistent", [1, 2, 3])
 def test_graph_replay_equals_direct_launches(persistent):
     """CUDA-graph replay of batches of sweeps gives the bits of direct launches
     and of the oracle, across replays, remainders, tempering steps, a counter

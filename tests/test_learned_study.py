@@ -16,10 +16,18 @@ pytestmark = pytest.mark.gpu
 def test_learned_ladder_study_gains_over_the_uniform_ladder(tmp_path):
     pytest.importorskip("torch")
     from paper_2310_07486_gb300 import ladder, workloads
-    out = ladder.study_main(workloads.ladder_study(), log=lambda *a: None)
+    st = workloads.ladder_study()
+    out = ladder.study_main(st, seeds=[st.seeds[0]], log=lambda *a: None)
     (tmp_path / "ladder_study.json").write_text(json.dumps(out))
-    print(json.dumps(out))
-    assert out["train_loss_first_last"][1] < out["train_loss_first_last"][0]
-    assert out["plain"]["passed"] > 0.5 and out["learned"]["passed"] >= out["plain"]["passed"] - 0.02
-    # fewer GPU-seconds per sample to pass the judge than the uniform ladder
-    assert out["gain"] > 1.0, out
+    print(json.dumps({k: v for k, v in out.items() if k != "per_seed"}))
+    one = out["per_seed"][0]
+    assert one["train_loss_first_last"][1] < one["train_loss_first_last"][0]
+    # more samples reach the judge's criterion within the cap with the learned ladders
+    assert out["learned_passed"] > out["plain_passed"]
+    # fewer GPU-seconds per thermalised sample: the lower end of the paired
+    # bootstrap interval (resampled evaluation samples) is above 1
+    assert out["gain_interval95"][0] > 1.0, out
+    # the size input carries the budget's growth with the lattice size
+    by_size = out["budget_by_training_size"]
+    pred = [b["pred_mean_log2_budget"] for b in by_size]
+    assert pred == sorted(pred)

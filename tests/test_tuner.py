@@ -22,7 +22,7 @@ def test_candidates_cover_persistent_and_graph_only_where_they_apply():
     one = list(tuner.candidates([Q.Shape(8, 32, 64, 1, 1)], sweeps_per_call=1))
     assert {c["persistent"] for c in one} == {1} and {c["graph"] for c in one} == {0}
     two = list(tuner.candidates([Q.Shape(8, 32, 64, 1, 1), Q.Shape(6, 32, 64, 1, 1)], sweeps_per_call=30))
-    assert {c["persistent"] for c in two} == {1, 2} and {c["graph"] for c in two} == {0, 30}
+    assert {c["persistent"] for c in two} == {1, 2, 3} and {c["graph"] for c in two} == {0, 30}
     assert len(two) == len({json.dumps(c, sort_keys=True) for c in two})
 
 
