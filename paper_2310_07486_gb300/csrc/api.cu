@@ -755,16 +755,14 @@ qsg_status qsg_set_spins(qsg_ctx *ctx, int32_t group, const uint64_t *host) {
 qsg_status qsg_get_spins_device(qsg_ctx *ctx, int32_t group, uint64_t *d_out) {
     if (!ctx || !d_out || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
     const Group &g = ctx->groups[group];
-    QSG_CUDA(ctx, cudaMemcpyAsync(d_out, g.S, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyDeviceToDevice,
-                                  ctx->stream));
+    QSG_CUDA(ctx, launch_copy_words(d_out, g.S, (size_t)g.nslots * g.N, ctx->stream));
     return QSG_OK;
 }
 
 qsg_status qsg_set_spins_device(qsg_ctx *ctx, int32_t group, const uint64_t *d_words) {
     if (!ctx || !d_words || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
     const Group &g = ctx->groups[group];
-    QSG_CUDA(ctx, cudaMemcpyAsync(g.S, d_words, sizeof(uint64_t) * (size_t)g.nslots * g.N, cudaMemcpyDeviceToDevice,
-                                  ctx->stream));
+    QSG_CUDA(ctx, launch_copy_words(g.S, d_words, (size_t)g.nslots * g.N, ctx->stream));
     ctx->energy_fresh = false;
     return QSG_OK;
 }

@@ -81,6 +81,22 @@ __global__ void k_half_sweep_ref(Group g, int colour, uint32_t sweep, uint32_t k
     }
 }
 
+// Device-to-device copy of spin state in 16-byte words (the copy engines move
+// device memory at a fraction of what the SMs' loads and stores reach).
+__global__ void k_copy16(uint4 *__restrict__ dst, const uint4 *__restrict__ src, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = __ldcs(src + i);
+}
+
+cudaError_t launch_copy_words(uint64_t *dst, const uint64_t *src, size_t words, cudaStream_t st) {
+    if (words == 0) return cudaSuccess;
+    if ((((uintptr_t)dst | (uintptr_t)src) & 15u) != 0 || (words & 1u) != 0)
+        return cudaMemcpyAsync(dst, src, words * sizeof(uint64_t), cudaMemcpyDeviceToDevice, st);
+    count_launches(1);
+    k_copy16<<<152 * 8, 512, 0, st>>>(reinterpret_cast<uint4 *>(dst), reinterpret_cast<const uint4 *>(src), words / 2);
+    return cudaGetLastError();
+}
+
 // Device copy of the sweep counter used by replayed graphs: set from the host
 // value before the first replay, advanced by the last node of each replay.
 __global__ void k_set_word(uint32_t *p, uint32_t v, int add) { *p = add ? *p + v : v; }

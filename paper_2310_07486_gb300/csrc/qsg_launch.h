@@ -48,6 +48,9 @@ cudaError_t launch_sweep_unit(const Group &g, int planes_per_barrier, int C, int
                               const uint32_t *sweep_base, uint32_t sweep, uint64_t seed, unsigned *arrivals,
                               cudaStream_t st);
 cudaError_t launch_set_word(uint32_t *p, uint32_t value, cudaStream_t st);
+// dst[0..words) = src[0..words), device to device, by a kernel when both are
+// 16-byte aligned and words is even (else by cudaMemcpyAsync).
+cudaError_t launch_copy_words(uint64_t *dst, const uint64_t *src, size_t words, cudaStream_t st);
 cudaError_t launch_add_word(uint32_t *p, uint32_t value, cudaStream_t st);
 
 // All groups of a context in one persistent launch per sweep (same algorithm,
