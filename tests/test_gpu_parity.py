@@ -575,3 +575,30 @@ def test_device_buffer_checkpoint_resume_is_bit_exact():
     assert np.array_equal(ctx.qsg_get_spins(0), first)
     with pytest.raises(Q.QSGError):
         ctx.qsg_set_spins_device(0, saved[:-1])
+
+
+def test_ragged_workload_sampled_in_its_default_launch_form():
+    """The ragged 640-sample workload (five groups, L = 8 .. 24, L_tau = 128 ..
+    2048, uneven ladders, 6.47 GB) with one stream per group inside 6-sweep
+    graphs: after two graph replays, a tempering step and one more replay,
+    one sample of every group equals the oracle's run of that sample."""
+    w = workloads.ragged()
+    ctx = Q.Context(w.shapes)
+    ctx.qsg_init_samples(w.seed, w.ladders)
+    ctx.qsg_set_option(Q.OPT_PERSISTENT, 3)
+    ctx.qsg_set_option(Q.OPT_GRAPH, 6)
+    ctx.qsg_sweep(12)
+    ctx.qsg_tempering_swap()
+    ctx.qsg_sweep(6)
+    for gid, (s, lad) in enumerate(zip(w.shapes, w.ladders)):
+        sample = (37 * gid + 11) % s.n_samples
+        orc = oracle.OracleGroup(s.L, s.Ltau, 1, s.n_replicas, s.n_k, algo=s.algo, boundary=s.boundary,
+                                 group_id=gid, first_sample=sample)
+        orc.init(w.seed, lad)
+        orc.sweep(12)
+        orc.swap()
+        orc.sweep(6)
+        words = ctx.qsg_get_spins(gid).reshape(s.words, s.n_replicas, s.n_k, -1)
+        mine = (1 - 2 * ((words[sample // 64] >> np.uint64(sample % 64)) & np.uint64(1)).astype(np.int8))
+        assert np.array_equal(mine.reshape(orc.spins()[0].shape), orc.spins()[0]), gid
+        assert np.array_equal(ctx.qsg_read_accepts(gid)[sample], orc.accepts()[0]), gid
