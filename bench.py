@@ -430,22 +430,22 @@ def run_ours(args, rank, world, local):
 
 def ragged_sweeps(peak_gbs, reps=4, batch=30):
     """The ragged workload (640 samples in five groups, L = 8 .. 24, L_tau =
-    128 .. 2048, 6.47 GB of state): sweeps of every group, device-timed with
-    CUDA events in each way of launching several groups (30-sweep CUDA
-    graphs): one launch per group in order, one persistent launch, one stream
-    per group."""
+    128 .. 2048, uneven ladders, 6.47 GB of state): sweeps of every group,
+    device-timed with CUDA events in each way of launching several groups
+    (30-sweep CUDA graphs: one launch per group in order, one persistent
+    launch, one stream per group), then in the launch form the tuner picks
+    over chunk, kernel form, multi-group mode and tail."""
     import torch
 
     from paper_2310_07486_gb300 import qsg as Q
+    from paper_2310_07486_gb300 import tuner
     from paper_2310_07486_gb300 import workloads
     w = workloads.ragged()
     ctx = Q.Context(w.shapes)
     ctx.qsg_init_samples(w.seed, w.ladders)
-    ctx.qsg_set_option(Q.OPT_GRAPH, batch)
     st = ctx.stream
-    ms = {}
-    for name, mode in (("sequential", 1), ("persistent", 2), ("concurrent", 3)):
-        ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
+
+    def time_it():
         ctx.qsg_sweep(batch)  # capture and warm-up
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -454,11 +454,21 @@ def ragged_sweeps(peak_gbs, reps=4, batch=30):
             ctx.qsg_sweep(batch)
         b.record(st)
         b.synchronize()
-        ms[name] = a.elapsed_time(b) / (reps * batch)
+        return a.elapsed_time(b) / (reps * batch)
+
+    ctx.qsg_set_option(Q.OPT_GRAPH, batch)
+    ms = {}
+    for name, mode in (("sequential", 1), ("persistent", 2), ("concurrent", 3)):
+        ctx.qsg_set_option(Q.OPT_PERSISTENT, mode)
+        ms[name] = time_it()
+    tuned = tuner.tune(ctx, sweeps_per_call=batch, reps=2,
+                       space={"graph": [batch], "chunk": [0, 64, 128], "variant": [0, 3]})
+    ms["tuned"] = time_it()
     best = min(ms, key=ms.get)
     gbs = 16 * w.words / (ms[best] * 1e-3) / 1e9
     ctx.close()
     return {"workload": w.name, "state_bytes": 8 * w.words, "ms_per_sweep": ms, "best": best,
+            "tuned_options": tuned["options"],
             "spin_flips_per_ns": w.spin_updates_per_sweep / (ms[best] * 1e6),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak_gbs, "unit": "GB/s", "frac": gbs / peak_gbs}}
 

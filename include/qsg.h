@@ -314,8 +314,8 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         0 = one work unit per block with L compiled in
  *                         (L = 20, 24; 72 registers, three blocks of 288
  *                         threads per SM at L = 24), four tau planes per
- *                         block barrier for heat bath and two for
- *                         Metropolis; other L use the generic kernel;
+ *                         block barrier; other L use the
+ *                         generic kernel;
  *                         1 = the same with two planes per barrier; 3 = with
  *                         four; 2 = the generic kernel (several units per
  *                         block, L at run time, two blocks per SM)

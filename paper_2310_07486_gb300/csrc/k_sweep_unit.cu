@@ -233,17 +233,19 @@ __global__ void __launch_bounds__(L *L / 2) __maxnreg__(NREG)
         QSG_C0_ODD(Q + 1, r.w)                                                                                  \
         cp_wait<2>();                                                                                           \
         __syncthreads();                                                                                        \
-        ra = draw(q + 2);                                                                                       \
         if (!EDGE || q >= a + 2) {                                                                              \
             QSG_C1_ODD(Q - 1, carry)                                                                            \
             QSG_C1_EVEN(Q, r.y)                                                                                 \
         }                                                                                                       \
+        ra = draw(q + 2);                                                                                       \
         if (!EDGE || q - 3 >= a) writeback(q - 3, QSG_SLOT(Q - 3));                                             \
         if (!EDGE || q - 2 >= a) writeback(q - 2, QSG_SLOT(Q - 2));                                             \
         carry = r.z;                                                                                            \
     }
 // four planes per barrier: the barrier waits for every group; planes q+10 ..
-// q+13 are issued after it, once planes q-5 .. q-2 have been written back
+// q+13 are issued after it, once planes q-5 .. q-2 have been written back.
+// The next step's random numbers are drawn after the colour-1 updates, when
+// this step's are dead (fewer live registers at 72)
 #define QSG_STEP4(MM)                                                                                           \
     {                                                                                                           \
         constexpr int Q = 4 * (MM);                                                                             \
@@ -259,14 +261,14 @@ __global__ void __launch_bounds__(L *L / 2) __maxnreg__(NREG)
         QSG_C0_ODD(Q + 3, rq1.w)                                                                                \
         cp_wait<0>();                                                                                           \
         __syncthreads();                                                                                        \
-        ra = draw(q + 4);                                                                                       \
-        rb = draw(q + 6);                                                                                       \
         if (!EDGE || q >= a + 4) {                                                                              \
             QSG_C1_ODD(Q - 1, carry)                                                                            \
             QSG_C1_EVEN(Q, rq0.y)                                                                               \
         }                                                                                                       \
         QSG_C1_ODD(Q + 1, rq0.z)                                                                                \
         QSG_C1_EVEN(Q + 2, rq1.y)                                                                               \
+        ra = draw(q + 4);                                                                                       \
+        rb = draw(q + 6);                                                                                       \
         if (!EDGE || q - 5 >= a) writeback(q - 5, QSG_SLOT(Q - 5));                                             \
         if (!EDGE || q - 4 >= a) writeback(q - 4, QSG_SLOT(Q - 4));                                             \
         if (!EDGE || q - 3 >= a) writeback(q - 3, QSG_SLOT(Q - 3));                                             \

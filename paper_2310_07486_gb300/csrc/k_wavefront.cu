@@ -473,9 +473,9 @@ cudaError_t launch_sweep_wavefront(const Group &g, const uint32_t *sweep_base, u
     // where that kernel exists, unless the generic kernel is asked for
     if (g_wavefront_variant != 2 && sweep_unit_supported(g)) {
         const int ts = tail_slots(g, C, tail);
-        // planes per barrier: the form that compiles with the fewest spills at
-        // 72 registers by default (4 for heat bath, 2 for Metropolis)
-        const int pb = g_wavefront_variant == 1 ? 2 : (g_wavefront_variant == 3 ? 4 : (g.algo == 1 ? 4 : 2));
+        // planes per barrier: four by default (the faster form for both
+        // algorithms), two as variant 1
+        const int pb = g_wavefront_variant == 1 ? 2 : 4;
         return launch_sweep_unit(g, pb, C, ts > 0 ? C / 4 : C, g.nslots - ts, sweep_base, sweep, seed, arrivals, st);
     }
     if (g.algo == 0) return launch_wf_algo<0>(g, C, tail, sweep_base, sweep, seed, arrivals, st);

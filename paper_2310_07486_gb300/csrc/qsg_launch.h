@@ -31,9 +31,8 @@ cudaError_t launch_sweep_reference(const Group &g, uint32_t sweep, uint64_t seed
 // The fused wavefront sweep: C = planes per work unit (0 if the group cannot
 // use this kernel), arrivals = nslots * (L_tau / 4) zeroed counters.
 int wavefront_chunk(const Group &g, int requested);
-// 0: one unit per block where k_sweep_unit exists (four planes per barrier
-// for heat bath, two for Metropolis); 1: two planes per barrier; 3: four;
-// 2: the generic kernel
+// 0: one unit per block where k_sweep_unit exists (four planes per
+// barrier); 1: two planes per barrier; 3: four (as 0); 2: the generic kernel
 extern int g_wavefront_variant;
 // The sweep index is *sweep_base + sweep (sweep_base may be null), so that a
 // captured CUDA graph of several sweeps can be replayed later.  The last

@@ -49,6 +49,12 @@ __device__ __forceinline__ uint64_t widen(uint32_t m) { return ((uint64_t)m << 3
 
 // One site update on multispin words.  Terms: nr/nl/nu/nd spatial neighbours
 // with couplings jr/jl/ju/jd, ntp/ntm time neighbours (APBC sign folded in).
+// b = the number of the six terms a_i (neighbour XOR coupling) that are 1.
+// Heat bath: the new spin is [b >= m].  Metropolis: with c the old spin the
+// unsatisfied bonds number b (c = 0) or 6 - b (c = 1), and the spin flips iff
+// that count is >= m; so the new spin is [b >= m] for c = 0 and
+// [6 - b < m] = [b >= 7 - m] for c = 1, and 7 - m = m XOR 7 for m <= 7: one
+// comparison [b >= m XOR 7c] with a threshold that differs per sample bit.
 template <int ALGO>
 __device__ __forceinline__ uint64_t update_site(uint64_t c, uint64_t nr, uint64_t nl, uint64_t nu, uint64_t nd,
                                                 uint64_t ntp, uint64_t ntm, uint64_t jr, uint64_t jl, uint64_t ju,
@@ -56,15 +62,17 @@ __device__ __forceinline__ uint64_t update_site(uint64_t c, uint64_t nr, uint64_
     uint64_t b0, b1, b2;
     uint32_t m0, m1, m2;
     threshold_masks<ALGO>(u, T, m0, m1, m2);
+    count6(nr ^ jr, nl ^ jl, nu ^ ju, nd ^ jd, ntp, ntm, b0, b1, b2);
+    if (ALGO == 0) {  // m <= 3: bit 2 of the threshold is c itself
+        const uint64_t t1 = widen(m1) ^ c;
+        const uint64_t e0 = b0 | ~(widen(m0) ^ c);
+        const uint64_t e1 = (b1 & ~t1) | (~(b1 ^ t1) & e0);
+        return (b2 & ~c) | (~(b2 ^ c) & e1);
+    }
     const uint64_t M0 = widen(m0), M1 = widen(m1), M2 = widen(m2);
-    if (ALGO == 0)
-        count6(c ^ nr ^ jr, c ^ nl ^ jl, c ^ nu ^ ju, c ^ nd ^ jd, c ^ ntp, c ^ ntm, b0, b1, b2);
-    else
-        count6(nr ^ jr, nl ^ jl, nu ^ ju, nd ^ jd, ntp, ntm, b0, b1, b2);
     const uint64_t e0 = b0 | ~M0;
     const uint64_t e1 = (b1 & ~M1) | (~(b1 ^ M1) & e0);
-    const uint64_t ge = (b2 & ~M2) | (~(b2 ^ M2) & e1);
-    return ALGO == 0 ? (c ^ ge) : ge;
+    return (b2 & ~M2) | (~(b2 ^ M2) & e1);
 }
 
 }  // namespace sweep

@@ -59,11 +59,17 @@ def candidate_chunks(shapes, largest=512):
     return out
 
 
-def candidates(shapes, sweeps_per_call):
-    chunks = candidate_chunks(shapes)
+def candidates(shapes, sweeps_per_call, space=None):
+    """Launch options to time; `space` may restrict any of "chunk",
+    "variant", "persistent", "graph" to a list of values."""
+    space = space or {}
+    chunks = [c for c in candidate_chunks(shapes) if c in space.get("chunk", [c])]
     persistent = [1, 2, 3] if len(shapes) > 1 else [1]
+    persistent = [p for p in persistent if p in space.get("persistent", [p])]
     graph = [0, sweeps_per_call] if sweeps_per_call > 1 else [0]
-    for chunk, variant, pers, gr in itertools.product(chunks, VARIANTS, persistent, graph):
+    graph = [g for g in graph if g in space.get("graph", [g])]
+    variants = [v for v in VARIANTS if v in space.get("variant", [v])]
+    for chunk, variant, pers, gr in itertools.product(chunks, variants, persistent, graph):
         yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0}
 
 
@@ -93,7 +99,7 @@ def _time_call(ctx, n_sweeps, reps):
     return best
 
 
-def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=True, verbose=False):
+def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=True, verbose=False, space=None):
     """Choose the fastest sweep launch options for ctx, apply them, and return
     ``{"options": {...}, "ms_per_sweep": t, "cached": bool, "table": [...]}``.
 
@@ -103,7 +109,8 @@ def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=Tr
     """
     import torch
     dev_name = torch.cuda.get_device_name(ctx.device)
-    key = cache_key(ctx.shapes, dev_name) + f"|{sweeps_per_call}"
+    key = cache_key(ctx.shapes, dev_name) + f"|{sweeps_per_call}" + (
+        "|" + json.dumps(space, sort_keys=True) if space else "")
     cache = {}
     if use_cache and cache_path and os.path.exists(cache_path):
         try:
@@ -120,7 +127,7 @@ def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=Tr
     counters = ctx.qsg_get_counters()
     table = []
     try:
-        for cand in candidates(ctx.shapes, sweeps_per_call):
+        for cand in candidates(ctx.shapes, sweeps_per_call, space):
             try:
                 apply(ctx, cand)
             except Q.QSGError:

@@ -26,6 +26,16 @@ def test_candidates_cover_persistent_and_graph_only_where_they_apply():
     assert len(two) == len({json.dumps(c, sort_keys=True) for c in two})
 
 
+def test_candidates_restricted_to_a_space():
+    shapes = [Q.Shape(8, 128, 64, 1, 1), Q.Shape(24, 2048, 64, 1, 1)]
+    space = {"graph": [30], "chunk": [0, 64, 128, 999], "variant": [0, 3]}
+    got = list(tuner.candidates(shapes, sweeps_per_call=30, space=space))
+    assert {c["chunk"] for c in got} == {0, 64, 128}  # 999 is not a valid chunk
+    assert {c["variant"] for c in got} == {0, 3} and {c["graph"] for c in got} == {30}
+    assert {c["persistent"] for c in got} == {1, 2, 3}
+    assert len(got) == 3 * 2 * 3
+
+
 @pytest.mark.gpu
 def test_tuned_context_samples_the_same_bits(tmp_path):
     torch = pytest.importorskip("torch")
