@@ -14,15 +14,21 @@
 // o > L_tau/2; o = L_tau/2 counts twice.
 //
 // One persistent CTA per SM, specialised warps:
-//   producers (8 warps, two threads per tile row) load the x-packed bit rows
-//     of the transposed scratch one row block ahead into registers and expand
-//     them to E4M3 +-1 (0 for padding) in shared memory, K-major with the
-//     128-byte swizzle, sites in a bit-interleaved order shared by A and B:
-//     the A row block once (resident, double buffered where shared memory
-//     allows, while its row of tiles is multiplied), B in 128-site chunks
-//     through a ring of stages;
-//   one thread issues the MMAs into two tensor-memory accumulators, so the
-//     next tile is multiplied while the last one is folded;
+//   producers (8 warps) load the x-packed bit rows of the transposed scratch
+//     one block ahead into registers and expand them to E4M3 +-1 (0 for
+//     padding) in shared memory, K-major with the 128-byte swizzle, sites in a
+//     bit-interleaved order shared by A and B: the row block A of an item in
+//     128-site chunks, each with its own full/empty barrier pair (so the next
+//     item's A is written chunk by chunk as the last tile of the current one
+//     releases it), and B two column blocks at a time in 32 KB stages (256
+//     rows x 128 sites);
+//   one thread issues the MMAs: the diagonal tile (i, i) with N = 128 and
+//     B = A, then the column-block pairs (i, j), (i, j + 1) as one N = 256
+//     MMA per 32-site step (a single block when the count is odd), into two
+//     256-column tensor-memory accumulators, so the next tile is multiplied
+//     while the last one is folded.  Issue is nearly synchronous with the
+//     tensor pipe, so the issuing thread does nothing between MMAs but wait
+//     for a stage every four of them;
 //   the epilogue (8 warps, two per TMEM lane quadrant) folds the tiles into
 //     shared-memory lag bins and flushes them to the int64 sums.
 // The work unit is one sample's row blocks i and nb - 1 - i: nb + 1 tiles for
@@ -37,8 +43,9 @@ constexpr int kTile = 128;                   // rows of A (t1) and of B (t2) per
 constexpr int kChunk = 128;                  // sites (bytes) per K chunk = one swizzled row
 constexpr int kChunkBytes = kTile * kChunk;  // 16 KB per operand chunk
 constexpr int kMaxNc = 8;                    // 128-site chunks of a row at most (L <= 32)
+constexpr int kStageBytes = 2 * kChunkBytes; // 32 KB per B stage (two column blocks)
 constexpr int kMaxStages = 6;                // B stages at most
-constexpr int kProducers = 256;              // warps 0-7: two threads per tile row
+constexpr int kProducers = 256;              // warps 0-7: one thread per B stage row
 constexpr int kProducerWarps = kProducers / 32;
 constexpr int kEpilogueWarps = 8;
 constexpr int kEpilogue = 256;               // warps 8-15: two per TMEM lane quadrant
@@ -59,14 +66,14 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor: D = FP32, A = B = E4M3, both K-major, M = N = 128.
-__device__ __forceinline__ uint32_t idesc_e4m3_128x128() {
-    return (1u << 4) | ((uint32_t)(kTile >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
+// Instruction descriptor: D = FP32, A = B = E4M3, both K-major, M = 128, N = n.
+__device__ __forceinline__ uint32_t idesc_e4m3(int n) {
+    return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTile >> 4) << 24);
 }
 
 struct Ctl {
     uint64_t bfull[kMaxStages], bempty[kMaxStages];  // B stage written / multiplied
-    uint64_t afull[2], aempty[2];                    // A buffer written / multiplied
+    uint64_t afull[kMaxNc], aempty[kMaxNc];          // A chunk written / multiplied
     uint64_t accfull[2], accempty[2];                // accumulator computed / folded
     uint64_t done;                                   // every MMA of the CTA completed
     uint32_t tmem;
@@ -74,11 +81,11 @@ struct Ctl {
 };
 
 // Wait for the phase of the given parity; false (and the abort flag set) when
-// `limit` polls are used up or another thread has given up already.
+// `limit` polls are used up, or when another thread has given up already (the
+// flag is read every 64 polls, after the barrier itself).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *abort, unsigned limit) {
-    volatile int *ab = abort;
-    if (*ab) return false;
     const uint32_t a = smem_u32(bar);
+    volatile int *ab = abort;
     for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
@@ -86,7 +93,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *a
                      : "r"(a), "r"(parity)
                      : "memory");
         if (done) return true;
-        if ((it & 255u) == 255u && *ab) return false;
+        if ((it & 63u) == 63u && *ab) return false;
     }
     *ab = 1;
     return false;
@@ -157,56 +164,6 @@ __device__ __forceinline__ void expand_word(uint8_t *rowp, uint64_t wv, int vali
         expand_part(rowp, wv, valid, hh, row);
 }
 
-// The work of one CTA: units u = blockIdx.x + n gridDim.x; unit u is sample
-// u / nhalf, row blocks h = u % nhalf and nb - 1 - h (one block when equal).
-// Within a unit the blocks are items; item i has the tiles (i, jb), jb >= i.
-// The producers' block sequence per item: the A block i, then the B blocks
-// jb = i+1..nb-1 (tile (i, i) takes B = A).
-struct Blk {
-    int u, sidx, h, item, i, jb;
-    bool valid;
-};
-
-__device__ __forceinline__ int item_block(int h, int item, int nb) { return item ? nb - 1 - h : h; }
-__device__ __forceinline__ int unit_items(int h, int nb) { return nb - 1 - h != h ? 2 : 1; }
-
-__device__ __forceinline__ void blk_unit(Blk &c, int nunits, int nhalf) {
-    c.valid = c.u < nunits;
-    c.sidx = c.u / nhalf;
-    c.h = c.u - c.sidx * nhalf;
-    c.item = 0;
-    c.i = c.h;
-    c.jb = c.h;
-}
-
-__device__ __forceinline__ void blk_first(Blk &c, int nunits, int nhalf) {
-    c.u = blockIdx.x;
-    blk_unit(c, nunits, nhalf);
-}
-
-__device__ __forceinline__ void blk_next(Blk &c, int nunits, int nhalf, int nb) {
-    if (++c.jb < nb) return;
-    if (++c.item >= unit_items(c.h, nb)) {
-        c.u += gridDim.x;
-        blk_unit(c, nunits, nhalf);
-        return;
-    }
-    c.i = item_block(c.h, c.item, nb);
-    c.jb = c.i;
-}
-
-// Bit words of thread (row, hh) in a block: w[kc] = word 2 kc + hh of row
-// jb * 128 + row, 0 outside the lattice and past L_tau.
-__device__ __forceinline__ void load_blk(const Blk &c, const uint64_t *__restrict__ P, int Lt, int nwx, int nc, int row,
-                                         int hh, uint64_t (&w)[kMaxNc]) {
-    const int t = c.jb * kTile + row;
-    const bool in = c.valid && t < Lt;
-    const uint64_t *src = P + ((size_t)(c.valid ? c.sidx : 0) * Lt + (t < Lt ? t : 0)) * nwx + hh;
-#pragma unroll
-    for (int kc = 0; kc < kMaxNc; ++kc)
-        if (kc < nc) w[kc] = (in && 2 * kc + hh < nwx) ? __ldg(src + 2 * kc) : 0ull;
-}
-
 // FP32 accumulator holding an integer |x| < 2^22 -> int32 with one add: in
 // [2^23, 2^24) the FP32 spacing is 1, so x + 1.5 * 2^23 is exact and its bit
 // pattern is that of 1.5 * 2^23 plus x.
@@ -214,22 +171,175 @@ __device__ __forceinline__ int exact_f32_to_int(uint32_t bits) {
     return __float_as_int(__uint_as_float(bits) + 12582912.0f) - 0x4B400000;
 }
 
+
+__device__ __forceinline__ void mma_f8(uint32_t d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+                 "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+// The work of one CTA: units u = blockIdx.x + n gridDim.x; unit u is sample
+// u / nhalf, row blocks h = u % nhalf and nb - 1 - h (one block when equal).
+// Within a unit the blocks are items; item i has the diagonal tile (i, i) and
+// the column-block pairs (i, jp), (i, jp + 1), jp = i + 1, i + 3, ...
+__device__ __forceinline__ int item_block(int h, int item, int nb) { return item ? nb - 1 - h : h; }
+__device__ __forceinline__ int unit_items(int h, int nb) { return nb - 1 - h != h ? 2 : 1; }
+
+// The producers' block sequence: per item the A block i, then the pairs.
+struct Seq {
+    int u, sidx, h, item, i, jp;
+    bool isA, valid;
+};
+
+__device__ __forceinline__ void seq_unit(Seq &c, int nunits, int nhalf) {
+    c.valid = c.u < nunits;
+    c.sidx = c.u / nhalf;
+    c.h = c.u - c.sidx * nhalf;
+    c.item = 0;
+    c.i = c.h;
+    c.isA = true;
+    c.jp = c.h;
+}
+
+__device__ __forceinline__ void seq_next(Seq &c, int nunits, int nhalf, int nb) {
+    if (c.isA) {
+        c.isA = false;
+        c.jp = c.i + 1;
+        if (c.jp < nb) return;
+    } else {
+        c.jp += 2;
+        if (c.jp < nb) return;
+    }
+    if (++c.item >= unit_items(c.h, nb)) {
+        c.u += gridDim.x;
+        seq_unit(c, nunits, nhalf);
+        return;
+    }
+    c.i = item_block(c.h, c.item, nb);
+    c.isA = true;
+    c.jp = c.i;
+}
+
+// Bit words of producer thread pt for block c, 0 outside the lattice and past
+// L_tau.  A block: w[kc] = word 2 kc + (pt >> 7) of row (pt & 127) of block
+// i.  Pair: w[2 kc + hh] = word 2 kc + hh of stage row pt (rows 0..127 are
+// block jp, rows 128..255 block jp + 1).
+template <int NC>
+__device__ __forceinline__ void load_seq(const Seq &c, const uint64_t *__restrict__ P, int Lt, int nwx, int pt,
+                                         uint64_t (&w)[2 * NC]) {
+    const size_t sbase = (size_t)(c.valid ? c.sidx : 0) * Lt;
+    if (c.isA) {
+        const int row = pt & 127, hh = pt >> 7;
+        const int t = c.i * kTile + row;
+        const bool in = c.valid && t < Lt;
+        const uint64_t *src = P + (sbase + (in ? t : 0)) * nwx + hh;
+#pragma unroll
+        for (int kc = 0; kc < NC; ++kc) w[kc] = (in && 2 * kc + hh < nwx) ? __ldg(src + 2 * kc) : 0ull;
+    } else {
+        const int t = (c.jp + (pt >> 7)) * kTile + (pt & 127);
+        const bool in = c.valid && t < Lt;
+        const uint64_t *src = P + (sbase + (in ? t : 0)) * nwx;
+#pragma unroll
+        for (int kc = 0; kc < NC; ++kc)
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh)
+                w[2 * kc + hh] = (in && 2 * kc + hh < nwx) ? __ldg(src + 2 * kc + hh) : 0ull;
+    }
+}
+
+// Fold the 64 columns cbase .. cbase + 63 of row m of tile (i, jb) into the
+// lag bins.  Most tiles map every element to lag o (all o < L_tau/2) or to
+// lag L_tau - o (all o > L_tau/2); only the tiles around L_tau/2 and those
+// past L_tau need the per-element choice.
+__device__ __forceinline__ void fold_slice(const uint32_t (&v)[64], int i, int jb, int m, int cbase, int Lt, int half,
+                                           int boundary, int *binC, unsigned *binQ) {
+    const int whigh = boundary == 1 ? -1 : 1;
+    const int t1 = i * kTile + m;
+    const int obase = (jb - i) * kTile;
+    const int omin = jb == i ? 1 : obase - (kTile - 1), omax = obase + kTile - 1;
+    const bool full = (jb + 1) * kTile <= Lt && (i + 1) * kTile <= Lt;
+    const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
+    const int o0 = obase + cbase - m;  // offset of column q is o0 + q
+    if (full && cls == 0 && jb != i) {
+        int *bc = binC + o0;
+        unsigned *bq = binQ + o0;
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+            const int gv = exact_f32_to_int(v[q]);
+            atomicAdd(bc + q, gv);
+            atomicAdd(bq + q, (unsigned)(gv * gv));
+        }
+    } else if (full && cls == 1) {
+        // the wrapped forward pair: lag L_tau - o0 - q (APBC: C takes the minus sign)
+        int *bc = binC + (Lt - o0);
+        unsigned *bq = binQ + (Lt - o0);
+        if (whigh == 1) {
+#pragma unroll
+            for (int q = 0; q < 64; ++q) {
+                const int gv = exact_f32_to_int(v[q]);
+                atomicAdd(bc - q, gv);
+                atomicAdd(bq - q, (unsigned)(gv * gv));
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 64; ++q) {
+                const int gv = exact_f32_to_int(v[q]);
+                atomicAdd(bc - q, -gv);
+                atomicAdd(bq - q, (unsigned)(gv * gv));
+            }
+        }
+    } else if (t1 < Lt) {
+#pragma unroll
+        for (int q = 0; q < 64; ++q) {
+            const int t2 = jb * kTile + cbase + q;
+            const int o = o0 + q;
+            if (t2 < Lt && o > 0) {
+                const int gv = exact_f32_to_int(v[q]);
+                int lag, wc, wq;
+                if (o < half) {
+                    lag = o; wc = 1; wq = 1;
+                } else if (o == half) {
+                    lag = half; wc = boundary == 1 ? 0 : 2; wq = 2;
+                } else {
+                    lag = Lt - o; wc = whigh; wq = 1;
+                }
+                atomicAdd(&binC[lag], wc * gv);
+                atomicAdd(&binQ[lag], (unsigned)(wq * gv * gv));
+            }
+        }
+    }
+}
+
+// 64 consecutive accumulator columns of the warp's 32 lanes
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+#pragma unroll
+    for (int c = 0; c < 64; c += 16)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+            : "=r"(v[c + 0]), "=r"(v[c + 1]), "=r"(v[c + 2]), "=r"(v[c + 3]), "=r"(v[c + 4]), "=r"(v[c + 5]),
+              "=r"(v[c + 6]), "=r"(v[c + 7]), "=r"(v[c + 8]), "=r"(v[c + 9]), "=r"(v[c + 10]), "=r"(v[c + 11]),
+              "=r"(v[c + 12]), "=r"(v[c + 13]), "=r"(v[c + 14]), "=r"(v[c + 15])
+            : "r"(taddr + (uint32_t)c));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
 }  // namespace
 
 // P: [sample][Ltau][nwx] transposed bits of the batch (sample = (pair, r, bit)).
+// NC = 128-site chunks of a row (L^2 / 128 rounded up).
+template <int NC>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int nabuf, int *status,
+    k_gram_tc(Group g, int p0, const uint64_t *__restrict__ P, int nsamples, int nstages, int *status,
               unsigned wait_limit) {
     extern __shared__ __align__(16) uint8_t dyn_raw[];
     uint8_t *dyn = dyn_raw + ((1024u - (smem_u32(dyn_raw) & 1023u)) & 1023u);
     __shared__ Ctl ctl;
     const int Lt = g.Ltau, L2 = g.L * g.L, half = Lt / 2, nl = g.nlag, nwx = g.nwx;
     const int nb = (Lt + kTile - 1) / kTile, nhalf = (nb + 1) / 2;
-    const int nc = (L2 + kChunk - 1) / kChunk;
     const int nunits = nsamples * nhalf;
-    uint8_t *sA = dyn;
-    uint8_t *sB = sA + (size_t)nabuf * nc * kChunkBytes;  // A buffers, then the B stages
-    int *binC = reinterpret_cast<int *>(sB + (size_t)nstages * kChunkBytes);
+    uint8_t *sA = dyn;                            // NC chunks of 128 rows x 128 sites
+    uint8_t *sB = sA + (size_t)NC * kChunkBytes;  // stages of 256 rows x 128 sites
+    int *binC = reinterpret_cast<int *>(sB + (size_t)nstages * kStageBytes);
     unsigned *binQ = reinterpret_cast<unsigned *>(binC + nl);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -238,9 +348,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.bfull[s])), "r"(kProducerWarps));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.bempty[s])));
         }
-        for (int b = 0; b < 2; ++b) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.afull[b])), "r"(kProducerWarps));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.aempty[b])));
+        for (int k = 0; k < kMaxNc; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(&ctl.afull[k])), "r"(kProducerWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.aempty[k])));
         }
         for (int a = 0; a < 2; ++a) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&ctl.accfull[a])));
@@ -251,7 +361,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ctl.abort = 0;
     }
     if (warp == kMmaWarp) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(&ctl.tmem)));
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(&ctl.tmem)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     for (int l = tid; l < nl; l += kThreads) {
@@ -263,148 +373,89 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     const uint32_t tmem = ctl.tmem;
 
-    if (warp < kProducers / 32) {
+    if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
-        // thread (row, hh): sites 64 hh .. 64 hh + 63 of every 128-site chunk of
-        // a tile row; the bit words of the next block are loaded into registers
-        // while the current block is expanded
-        const int row = tid >> 1, hh = tid & 1;
-        Blk cur, nxt;
-        blk_first(cur, nunits, nhalf);
-        uint64_t wc[kMaxNc], wn[kMaxNc];
-        load_blk(cur, P, Lt, nwx, nc, row, hh, wc);
-        // aempty / bempty[s] parities: the first use of a buffer waits for the
-        // phase before the first (complete at initialisation)
-        uint32_t a_par = 3u, b_par = 1u;  // a_par: bit b = parity of A buffer b
-        int s = 0, ab = 0;
+        // the bit words of the next block are loaded into registers while the
+        // current one is expanded; one chunk loop serves both kinds of block
+        // (one inline expansion per chunk keeps the code small): an A block's
+        // thread writes word tid >> 7 of row tid & 127, a pair block's thread
+        // both words of stage row tid (none past a single last block)
+        Seq cur, nxt;
+        cur.u = blockIdx.x;
+        seq_unit(cur, nunits, nhalf);
+        uint64_t wc[2 * NC], wn[2 * NC];
+        load_seq<NC>(cur, P, Lt, nwx, tid, wc);
+        // the first use of a buffer waits for the phase before the first
+        // (complete at initialisation)
+        uint32_t a_ph = 1u, b_par = 1u;
+        int s = 0;
         while (cur.valid) {
             nxt = cur;
-            blk_next(nxt, nunits, nhalf, nb);
-            load_blk(nxt, P, Lt, nwx, nc, row, hh, wn);
-            const int t = cur.jb * kTile + row;
-            const bool isA = cur.jb == cur.i;  // the A block of an item
-            uint8_t *abuf = sA + (size_t)ab * nc * kChunkBytes + row * kChunk;
+            seq_next(nxt, nunits, nhalf, nb);
+            load_seq<NC>(nxt, P, Lt, nwx, tid, wn);
+            const bool isA = cur.isA;
+            const bool pair = cur.jp + 1 < nb;
+            const int row = isA ? (tid & 127) : tid, hh0 = isA ? (tid >> 7) : 0;
+            const int nw = isA ? 1 : ((pair || tid < kTile) ? 2 : 0);
+            const int t = isA ? cur.i * kTile + row : (cur.jp + (tid >> 7)) * kTile + (tid & 127);
 #pragma unroll
-            for (int kc = 0; kc < kMaxNc; ++kc) {
-                if (kc < nc) {
-                    bool ok = true;
-                    if (!isA)
-                        ok = mbar_wait(&ctl.bempty[s], b_par, &ctl.abort, wait_limit);
-                    else if (kc == 0)
-                        ok = mbar_wait(&ctl.aempty[ab], (a_par >> ab) & 1u, &ctl.abort, wait_limit);
-                    uint8_t *rowp = isA ? abuf + (size_t)kc * kChunkBytes : sB + (size_t)s * kChunkBytes + row * kChunk;
-                    if (ok) expand_word(rowp, wc[kc], t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
-                    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                    __syncwarp();  // the warp's rows are written: one arrival per warp
-                    if (!isA) {
-                        if (lane == 0) mbar_arrive(&ctl.bfull[s]);
-                        if (++s == nstages) {
-                            s = 0;
-                            b_par ^= 1u;
-                        }
-                    } else if (kc == nc - 1) {
-                        if (lane == 0) mbar_arrive(&ctl.afull[ab]);
-                        a_par ^= 1u << ab;
-                        if (++ab == nabuf) ab = 0;
+            for (int kc = 0; kc < NC; ++kc) {
+                const bool ok = isA ? mbar_wait(&ctl.aempty[kc], a_ph, &ctl.abort, wait_limit)
+                                    : mbar_wait(&ctl.bempty[s], b_par, &ctl.abort, wait_limit);
+                uint8_t *rowp = isA ? sA + (size_t)kc * kChunkBytes + row * kChunk
+                                    : sB + (size_t)s * kStageBytes + row * kChunk;
+                const uint64_t w0 = isA ? wc[kc] : wc[2 * kc], w1 = wc[2 * kc + 1];
+                if (ok) {
+#pragma unroll 1
+                    for (int k = 0; k < nw; ++k) {
+                        const int hh = hh0 + k;
+                        expand_word(rowp, k ? w1 : w0, t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
                     }
                 }
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                __syncwarp();  // the warp's rows are written: one arrival per warp
+                if (lane == 0) mbar_arrive(isA ? &ctl.afull[kc] : &ctl.bfull[s]);
+                if (!isA && ++s == nstages) {
+                    s = 0;
+                    b_par ^= 1u;
+                }
             }
+            if (isA) a_ph ^= 1u;
 #pragma unroll
-            for (int kc = 0; kc < kMaxNc; ++kc) wc[kc] = wn[kc];
+            for (int k = 0; k < 2 * NC; ++k) wc[k] = wn[k];
             cur = nxt;
         }
     } else if (warp < kMmaWarp) {
         // ------------------------------------------------------------- epilogue
         const int etid = tid - kProducers;
-        const int quad = warp & 3;                       // TMEM lanes 32 quad .. 32 quad + 31
-        const int cbase = ((warp - kProducers / 32) >> 2) * 64;  // column half of the tile
-        const int m = quad * 32 + lane;                  // tile row
-        const int whigh = g.boundary == 1 ? -1 : 1;
+        const int quad = warp & 3;                                  // TMEM lanes 32 quad .. 32 quad + 31
+        const int cbase = ((warp - kProducerWarps) >> 2) * 64;     // column half of a 128-column tile
+        const int m = quad * 32 + lane;                             // tile row
         uint32_t n_t = 0;
         for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
             const int sidx = u / nhalf, h = u % nhalf;
             for (int item = 0; item < unit_items(h, nb); ++item) {
                 const int i = item_block(h, item, nb);
-                const int t1 = i * kTile + m;
-                for (int jb = i; jb < nb; ++jb, ++n_t) {
+                // the MMA's tile order: (i, i), then the pairs from jp = i + 1
+                for (int jp = i; jp < nb; jp = (jp == i ? i + 1 : jp + 2), ++n_t) {
+                    const int nsub = (jp != i && jp + 1 < nb) ? 2 : 1;
                     const int a = (int)(n_t & 1u);
-                    const bool ok = mbar_wait(&ctl.accfull[a], (n_t >> 1) & 1u, &ctl.abort, wait_limit);
+                    // warp-uniform: the tensor-memory loads below are .sync.aligned
+                    const bool ok =
+                        __all_sync(0xFFFFFFFFu, mbar_wait(&ctl.accfull[a], (n_t >> 1) & 1u, &ctl.abort, wait_limit));
                     asm volatile("tcgen05.fence::after_thread_sync;\n");
                     if (ok) {
-                        // offsets o = t2 - t1 of this tile lie in [omin, omax]; most
-                        // tiles map every element to lag o (all o < L_tau/2) or to lag
-                        // L_tau - o (all o > L_tau/2), only the tiles around L_tau/2
-                        // need the per-element choice
-                        const int obase = (jb - i) * kTile;
-                        const int omin = jb == i ? 1 : obase - (kTile - 1), omax = obase + kTile - 1;
-                        const bool full = (jb + 1) * kTile <= Lt && (i + 1) * kTile <= Lt;
-                        const int cls = (omax < half) ? 0 : (omin > half ? 1 : 2);
-                        uint32_t v[64];
-                        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * kTile + cbase);
-#pragma unroll
-                        for (int c = 0; c < 64; c += 16)
-                            asm volatile(
-                                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-                                : "=r"(v[c + 0]), "=r"(v[c + 1]), "=r"(v[c + 2]), "=r"(v[c + 3]), "=r"(v[c + 4]),
-                                  "=r"(v[c + 5]), "=r"(v[c + 6]), "=r"(v[c + 7]), "=r"(v[c + 8]), "=r"(v[c + 9]),
-                                  "=r"(v[c + 10]), "=r"(v[c + 11]), "=r"(v[c + 12]), "=r"(v[c + 13]), "=r"(v[c + 14]),
-                                  "=r"(v[c + 15])
-                                : "r"(taddr + (uint32_t)c));
-                        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-                        // the accumulator is free for the tile after next
-                        asm volatile("tcgen05.fence::before_thread_sync;\n");
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&ctl.accempty[a]);
-                        const int o0 = obase + cbase - m;  // offset of column q is o0 + q
-                        if (full && cls == 0 && jb != i) {
-                            // every element folds to lag o0 + q (all o < L_tau/2)
-                            int *bc = binC + o0;
-                            unsigned *bq = binQ + o0;
-#pragma unroll
-                            for (int q = 0; q < 64; ++q) {
-                                const int gv = exact_f32_to_int(v[q]);
-                                atomicAdd(bc + q, gv);
-                                atomicAdd(bq + q, (unsigned)(gv * gv));
+                        for (int sub = 0; sub < nsub; ++sub) {
+                            uint32_t v[64];
+                            tmem_ld64(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * 256 + sub * kTile + cbase),
+                                      v);
+                            if (sub == nsub - 1) {
+                                // the accumulator is free for the tile after next
+                                asm volatile("tcgen05.fence::before_thread_sync;\n");
+                                __syncwarp();
+                                if (lane == 0) mbar_arrive(&ctl.accempty[a]);
                             }
-                        } else if (full && cls == 1) {
-                            // every element folds to lag L_tau - o0 - q, the wrapped
-                            // forward pair (APBC: C takes the minus sign)
-                            int *bc = binC + (Lt - o0);
-                            unsigned *bq = binQ + (Lt - o0);
-                            if (whigh == 1) {
-#pragma unroll
-                                for (int q = 0; q < 64; ++q) {
-                                    const int gv = exact_f32_to_int(v[q]);
-                                    atomicAdd(bc - q, gv);
-                                    atomicAdd(bq - q, (unsigned)(gv * gv));
-                                }
-                            } else {
-#pragma unroll
-                                for (int q = 0; q < 64; ++q) {
-                                    const int gv = exact_f32_to_int(v[q]);
-                                    atomicAdd(bc - q, -gv);
-                                    atomicAdd(bq - q, (unsigned)(gv * gv));
-                                }
-                            }
-                        } else if (t1 < Lt) {
-#pragma unroll
-                            for (int q = 0; q < 64; ++q) {
-                                const int t2 = jb * kTile + cbase + q;
-                                const int o = o0 + q;
-                                if (t2 < Lt && o > 0) {
-                                    const int gv = exact_f32_to_int(v[q]);
-                                    int lag, wc, wq;
-                                    if (o < half) {
-                                        lag = o; wc = 1; wq = 1;
-                                    } else if (o == half) {
-                                        lag = half; wc = g.boundary == 1 ? 0 : 2; wq = 2;
-                                    } else {
-                                        lag = Lt - o; wc = whigh; wq = 1;
-                                    }
-                                    atomicAdd(&binC[lag], wc * gv);
-                                    atomicAdd(&binQ[lag], (unsigned)(wq * gv * gv));
-                                }
-                            }
+                            fold_slice(v, i, jp + sub, m, cbase, Lt, half, g.boundary, binC, binQ);
                         }
                     } else {
                         asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -439,63 +490,75 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------------------------ MMA
-        const uint32_t idesc = idesc_e4m3_128x128();
-        uint32_t a_par = 0u, b_par = 0u, n_t = 0;
-        int bs = 0, ab = 0;
-        bool issued = false;
-        for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-            const int h = u % nhalf;
-            for (int item = 0; item < unit_items(h, nb); ++item) {
-                const int i = item_block(h, item, nb);
-                const bool a_ok = mbar_wait(&ctl.afull[ab], (a_par >> ab) & 1u, &ctl.abort, wait_limit);
-                const uint8_t *sAb = sA + (size_t)ab * nc * kChunkBytes;
-                asm volatile("tcgen05.fence::after_thread_sync;\n");
-                for (int jb = i; jb < nb; ++jb, ++n_t) {
-                    const int a = (int)(n_t & 1u);
-                    bool ok = a_ok && mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort, wait_limit);
-                    asm volatile("tcgen05.fence::after_thread_sync;\n");
-                    for (int kc = 0; kc < nc; ++kc) {
-                        const uint32_t abase = smem_u32(sAb + (size_t)kc * kChunkBytes);
-                        uint32_t bbase = abase;
-                        if (jb != i) {
+        // one thread issues every MMA; after the last tile of an item uses an
+        // A chunk, a commit frees that chunk for the next item's A block
+        if (lane == 0) {
+            const uint32_t id128 = idesc_e4m3(128), id256 = idesc_e4m3(256);
+            const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
+            uint32_t a_par = 0u, b_par = 0u, n_t = 0;
+            int bs = 0;
+            bool issued = false;
+            for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+                const int h = u % nhalf;
+                for (int item = 0; item < unit_items(h, nb); ++item) {
+                    const int i = item_block(h, item, nb);
+                    {  // the diagonal tile: B = A, 128 columns
+                        const bool last = i + 1 >= nb;
+                        const int a = (int)(n_t & 1u);
+                        bool ok = mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort, wait_limit);
+                        asm volatile("tcgen05.fence::after_thread_sync;\n");
+                        const uint32_t d = tmem + (uint32_t)(a * 256);
+#pragma unroll
+                        for (int kc = 0; kc < NC; ++kc) {
+                            ok = mbar_wait(&ctl.afull[kc], a_par, &ctl.abort, wait_limit) && ok;
+                            asm volatile("tcgen05.fence::after_thread_sync;\n");
+                            if (ok) {
+                                const uint32_t ab = sA0 + kc * kChunkBytes;
+#pragma unroll
+                                for (int kk = 0; kk < kChunk / 32; ++kk)
+                                    mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(ab + kk * 32), id128,
+                                           (kc > 0 || kk > 0) ? 1u : 0u);
+                                issued = true;
+                            }
+                            if (last) mma_commit(&ctl.aempty[kc]);
+                        }
+                        mma_commit(&ctl.accfull[a]);
+                        ++n_t;
+                    }
+                    for (int jp = i + 1; jp < nb; jp += 2) {  // column blocks jp and jp + 1
+                        const bool pair = jp + 1 < nb, last = jp + 2 >= nb;
+                        const int a = (int)(n_t & 1u);
+                        bool ok = mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort, wait_limit);
+                        asm volatile("tcgen05.fence::after_thread_sync;\n");
+                        const uint32_t d = tmem + (uint32_t)(a * 256);
+                        const uint32_t idesc = pair ? id256 : id128;
+#pragma unroll
+                        for (int kc = 0; kc < NC; ++kc) {
                             ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort, wait_limit) && ok;
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
-                            bbase = smem_u32(sB + (size_t)bs * kChunkBytes);
-                        }
-                        if (ok && lane == 0) {
+                            if (ok) {
+                                const uint32_t ab = sA0 + kc * kChunkBytes, bb = sB0 + bs * kStageBytes;
 #pragma unroll
-                            for (int kk = 0; kk < kChunk / 32; ++kk) {
-                                const uint64_t da = sdesc_sw128(abase + kk * 32);
-                                const uint64_t db = sdesc_sw128(bbase + kk * 32);
-                                const uint32_t acc = (kc > 0 || kk > 0) ? 1u : 0u;
-                                asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
-                                             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                                 tmem + (uint32_t)(a * kTile)),
-                                             "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                                for (int kk = 0; kk < kChunk / 32; ++kk)
+                                    mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(bb + kk * 32), idesc,
+                                           (kc > 0 || kk > 0) ? 1u : 0u);
+                                issued = true;
                             }
-                            issued = true;
-                        }
-                        if (jb != i) {
-                            if (lane == 0) mma_commit(&ctl.bempty[bs]);
+                            mma_commit(&ctl.bempty[bs]);
+                            if (last) mma_commit(&ctl.aempty[kc]);
                             if (++bs == nstages) {
                                 bs = 0;
                                 b_par ^= 1u;
                             }
                         }
-                        __syncwarp();
+                        mma_commit(&ctl.accfull[a]);
+                        ++n_t;
                     }
-                    if (lane == 0) mma_commit(&ctl.accfull[a]);
-                    __syncwarp();
+                    a_par ^= 1u;
                 }
-                if (lane == 0) mma_commit(&ctl.aempty[ab]);
-                __syncwarp();
-                a_par ^= 1u << ab;
-                if (++ab == nabuf) ab = 0;
             }
-        }
-        // every MMA issued has completed before the tensor memory is released
-        // (a commit tracks all earlier MMAs of the issuing thread)
-        if (lane == 0) {
+            // every MMA issued has completed before the tensor memory is released
+            // (a commit tracks all earlier MMAs of the issuing thread)
             mma_commit(&ctl.done);
             if (issued) {
                 uint32_t done = 0;
@@ -512,55 +575,64 @@ __global__ void __launch_bounds__(kThreads, 1)
     asm volatile("tcgen05.fence::before_thread_sync;\n");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n");
-    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+    if (warp == kMmaWarp) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
     if (tid == 0 && ctl.abort) atomicExch(status, DEVERR_TIMEOUT);
 }
 
 namespace {
 
-size_t gram_tc_smem_bytes(const Group &g, int nstages, int nabuf) {
-    const int nc = (g.L * g.L + kChunk - 1) / kChunk;
-    return 1024 + (size_t)(nabuf * nc + nstages) * kChunkBytes + 2 * sizeof(int) * (size_t)g.nlag;
-}
-
 constexpr size_t kSmemLimit = 227 * 1024 - 256;  // dynamic + the static control block
 
-// Shared-memory plan: two A buffers (the next row block is expanded while the
-// last tiles of the current one are multiplied) with at least four B stages
-// where that fits, else one A buffer; as many B stages as fit, up to six.
-struct TcPlan {
-    int nstages, nabuf;
-};
-
-TcPlan gram_tc_plan(const Group &g) {
-    for (int nabuf = 2; nabuf >= 1; --nabuf)
-        for (int s = kMaxStages; s >= (nabuf == 2 ? 4 : 2); --s)
-            if (gram_tc_smem_bytes(g, s, nabuf) <= kSmemLimit) return {s, nabuf};
-    return {0, 0};
+size_t gram_tc_smem_bytes(const Group &g, int nc, int nstages) {
+    return 1024 + (size_t)nc * kChunkBytes + (size_t)nstages * kStageBytes + 2 * sizeof(int) * (size_t)g.nlag;
 }
 
-}  // namespace
+// As many B stages as fit, up to six; at least two.
+int gram_tc_stages(const Group &g) {
+    const int nc = (g.L * g.L + kChunk - 1) / kChunk;
+    if (nc < 1 || nc > kMaxNc) return 0;
+    for (int s = kMaxStages; s >= 2; --s)
+        if (gram_tc_smem_bytes(g, nc, s) <= kSmemLimit) return s;
+    return 0;
+}
 
-bool gram_tc_fits(const Group &g) { return gram_tc_plan(g).nstages >= 2; }
-
-cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, unsigned wait_limit,
-                           cudaStream_t st) {
-    const TcPlan plan = gram_tc_plan(g);
-    if (plan.nstages < 2) return cudaErrorInvalidValue;
-    const size_t sm = gram_tc_smem_bytes(g, plan.nstages, plan.nabuf);
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+template <int NC>
+cudaError_t launch_nc(const Group &g, int p0, int nsamples, int nstages, const uint64_t *P, int *status,
+                      unsigned wait_limit, int nsm, cudaStream_t st) {
+    const size_t sm = gram_tc_smem_bytes(g, NC, nstages);
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    int dev = 0, nsm = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return e;
-    const int nsamples = npairs * g.R * 64;
     const int nb = (g.Ltau + kTile - 1) / kTile;
     const long long nunits = (long long)nsamples * ((nb + 1) / 2);
     const int grid = (int)(nunits < nsm ? nunits : nsm);
     count_launches(1);
-    k_gram_tc<<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, plan.nstages, plan.nabuf, status, wait_limit);
+    k_gram_tc<NC><<<grid, kThreads, sm, st>>>(g, p0, P, nsamples, nstages, status, wait_limit);
     return cudaGetLastError();
+}
+
+}  // namespace
+
+bool gram_tc_fits(const Group &g) { return gram_tc_stages(g) >= 2; }
+
+cudaError_t launch_gram_tc(const Group &g, int p0, int npairs, const uint64_t *P, int *status, unsigned wait_limit,
+                           cudaStream_t st) {
+    const int nstages = gram_tc_stages(g);
+    if (nstages < 2) return cudaErrorInvalidValue;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int nsamples = npairs * g.R * 64;
+    switch ((g.L * g.L + kChunk - 1) / kChunk) {
+        case 1: return launch_nc<1>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 2: return launch_nc<2>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 3: return launch_nc<3>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 4: return launch_nc<4>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 5: return launch_nc<5>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 6: return launch_nc<6>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        case 7: return launch_nc<7>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+        default: return launch_nc<8>(g, p0, nsamples, nstages, P, status, wait_limit, nsm, st);
+    }
 }
 
 }  // namespace qsg
