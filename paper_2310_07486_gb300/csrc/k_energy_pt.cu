@@ -4,11 +4,11 @@
 
 namespace qsg {
 
-constexpr int kEnergyPlanes = 16;
-constexpr int kEnergyRun = 128;                // tau planes per block (even)
-constexpr int kEnergyBuf = 8;                  // planes in the shared-memory ring
-constexpr int kEnergyAhead = kEnergyBuf - 3;   // planes in flight beyond the three being read
-constexpr int kEnergyFlush = 4;                // planes per carry-save group: 2 sites x 3 bonds x 4 <= 31
+constexpr int kEnergyPlanes = 16;              // bits of a warp's count per sample (32 x 6 x kEnergyRun < 2^15)
+constexpr int kEnergyRun = 128;                // tau planes per block (a multiple of 4)
+constexpr int kEnergyBuf = 16;                 // planes in the shared-memory ring
+constexpr int kEnergyAhead = kEnergyBuf - 5;   // planes in flight beyond the five being read
+constexpr int kEnergyThirtyTwos = 5;           // planes of a thread's count of 32s (6 x kEnergyRun / 32 < 2^5)
 
 // a += b for two bitsliced counters of kEnergyPlanes planes (ripple carry)
 __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const uint64_t (&b)[kEnergyPlanes]) {
@@ -21,33 +21,25 @@ __device__ __forceinline__ void vadd_counter(uint64_t (&a)[kEnergyPlanes], const
     }
 }
 
-// (o16 o8 o4 o2 o1) += the unsatisfied-bond count of one site: its three
-// bond words go through a full adder into sum + 2 car
-__device__ __forceinline__ void count_site(uint64_t ux, uint64_t uy, uint64_t ut, uint64_t &o1, uint64_t &o2,
-                                           uint64_t &o4, uint64_t &o8, uint64_t &o16) {
-    const uint64_t sum = ux ^ uy ^ ut, car = (ux & uy) | (ut & (ux ^ uy));
-    const uint64_t h1 = o1 & sum;
-    o1 ^= sum;
-    const uint64_t h2 = (o2 & car) | (h1 & (o2 ^ car));
-    o2 ^= car ^ h1;
-    const uint64_t h4 = o4 & h2;
-    o4 ^= h2;
-    const uint64_t h8 = o8 & h4;
-    o8 ^= h4;
-    o16 ^= h8;
+// carry-save adder: l = a ^ b ^ c (same weight), h = majority (twice the weight)
+__device__ __forceinline__ void csa(uint64_t &h, uint64_t &l, uint64_t a, uint64_t b, uint64_t c) {
+    const uint64_t u = a ^ b;
+    h = (a & b) | (u & c);
+    l = u ^ c;
 }
 
 // U[slot][b] += number of unsatisfied bonds (J S S' = -1) among the three
 // forward bonds (+x, +y, +tau) of every site; each bond is counted once and
 // E = -(3N - 2U) is the action of Eq. (Trotter-action).  A block covers one
-// slot over kEnergyRun planes, two planes per block barrier; its planes
+// slot over kEnergyRun planes, four planes per block barrier; its planes
 // stream through a ring of kEnergyBuf shared-memory planes filled by cp.async
 // kEnergyAhead planes ahead, so every word is read from HBM once and the +x,
-// +y and +tau neighbours come from shared memory.  A thread owns two adjacent site words
-// of a row; their bond counts go through a 5-bit carry-save accumulator,
-// added into the kEnergyPlanes-plane per-thread counter every kEnergyFlush
-// planes; the warp then sums its counters with shuffles and one lane turns
-// them into per-sample integers.
+// +y and +tau neighbours come from shared memory.  A thread owns two adjacent
+// site words of a row: six bond words per plane, 24 per step, summed per
+// sample bit by a Harley-Seal carry-save tree whose ones, twos, fours,
+// eights and sixteens are the low bit-planes of the thread's count (one
+// ripple into the count of 32s per step); the warp then sums its counters
+// with shuffles and one lane turns them into per-sample integers.
 __global__ void __launch_bounds__(512, 2) k_energy(Group g) {
     extern __shared__ __align__(16) uint64_t eplanes[];  // [kEnergyBuf][L^2]
     __shared__ int cnt[64];
@@ -86,9 +78,13 @@ __global__ void __launch_bounds__(512, 2) k_energy(Group g) {
     const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
 #pragma unroll
     for (int d = 0; d <= kEnergyAhead; ++d) issue(t0 + d);
-    uint64_t o1 = 0, o2 = 0, o4 = 0, o8 = 0, o16 = 0;
-    int ng = 0;
-    auto plane = [&](int q) {
+    // the six bond words of the thread's two sites on plane q (zero past t1)
+    auto bonds = [&](int q, uint64_t (&x)[6]) {
+        if (q >= t1) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) x[k] = 0;
+            return;
+        }
         const uint64_t *P = eplanes + (size_t)(q % kEnergyBuf) * L2;
         const uint64_t *Pn = eplanes + (size_t)((q + 1) % kEnergyBuf) * L2;
         const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(P + xy);
@@ -96,38 +92,70 @@ __global__ void __launch_bounds__(512, 2) k_energy(Group g) {
         const ulonglong2 n = *reinterpret_cast<const ulonglong2 *>(Pn + xy);
         const uint64_t r1 = P[xr];
         const uint64_t ft = q + 1 == Lt ? apbc : 0ull;
-        count_site(v.x ^ v.y ^ j0x, v.x ^ u.x ^ j0y, v.x ^ n.x ^ ft, o1, o2, o4, o8, o16);
-        count_site(v.y ^ r1 ^ j1x, v.y ^ u.y ^ j1y, v.y ^ n.y ^ ft, o1, o2, o4, o8, o16);
+        x[0] = v.x ^ v.y ^ j0x;
+        x[1] = v.x ^ u.x ^ j0y;
+        x[2] = v.x ^ n.x ^ ft;
+        x[3] = v.y ^ r1 ^ j1x;
+        x[4] = v.y ^ u.y ^ j1y;
+        x[5] = v.y ^ n.y ^ ft;
     };
-    for (int q = t0; q < t1; q += 2) {
-        // planes q, q + 1 and q + 2 have landed (q + 3 .. q + kEnergyAhead may be in flight)
-        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEnergyAhead - 2) : "memory");
+    uint64_t ones = 0, twos = 0, fours = 0, eights = 0, sixteens = 0;
+    // 12 bond words into ones / twos / fours; the two carries of weight 8 out
+    auto tree12 = [&](const uint64_t (&x)[6], const uint64_t (&y)[6], uint64_t &eA, uint64_t &eB) {
+        uint64_t tA, tB, tC, tD, tE, tF, fA, fB, fC;
+        csa(tA, ones, ones, x[0], x[1]);
+        csa(tB, ones, ones, x[2], x[3]);
+        csa(fA, twos, twos, tA, tB);
+        csa(tC, ones, ones, x[4], x[5]);
+        csa(tD, ones, ones, y[0], y[1]);
+        csa(fB, twos, twos, tC, tD);
+        csa(eA, fours, fours, fA, fB);
+        csa(tE, ones, ones, y[2], y[3]);
+        csa(tF, ones, ones, y[4], y[5]);
+        csa(fC, twos, twos, tE, tF);
+        eB = fours & fC;
+        fours ^= fC;
+    };
+    for (int q = t0; q < t1; q += 4) {
+        // planes q .. q + 4 have landed (q + 5 .. q + kEnergyAhead may be in flight)
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(kEnergyAhead - 4) : "memory");
         __syncthreads();
-        // the slots of planes q - 2 and q - 1 are free for every thread: refill them
+        // the slots of planes q - 4 .. q - 1 are free for every thread: refill them
         issue(q + kEnergyAhead + 1);
         issue(q + kEnergyAhead + 2);
+        issue(q + kEnergyAhead + 3);
+        issue(q + kEnergyAhead + 4);
         if (own) {
-            plane(q);
-            if (q + 1 < t1) plane(q + 1);
-        }
-        ng += 2;
-        if (ng == kEnergyFlush || q + 2 >= t1) {
-            // c += (o16 o8 o4 o2 o1): ripple over the low planes (a thread counts
-            // at most 6 * kEnergyRun < 2^10 per position)
-            uint64_t carry = 0;
-            const uint64_t in[5] = {o1, o2, o4, o8, o16};
+            uint64_t x[6], y[6], eA1, eB1, eA2, eB2;
+            bonds(q, x);
+            bonds(q + 1, y);
+            tree12(x, y, eA1, eB1);
+            bonds(q + 2, x);
+            bonds(q + 3, y);
+            tree12(x, y, eA2, eB2);
+            uint64_t s16a, s16b, c32;
+            csa(s16a, eights, eights, eA1, eB1);
+            csa(s16b, eights, eights, eA2, eB2);
+            csa(c32, sixteens, sixteens, s16a, s16b);
+            // count of 32s += c32 (a thread counts at most 6 x kEnergyRun < 2^10)
+            uint64_t carry = c32;
 #pragma unroll
-            for (int p = 0; p < 10; ++p) {
-                const uint64_t b = p < 5 ? in[p] : 0ull;
-                const uint64_t sp = c[p] ^ b ^ carry;
-                carry = (c[p] & b) | (carry & (c[p] ^ b));
-                c[p] = sp;
+            for (int p = 0; p < kEnergyThirtyTwos; ++p) {
+                const uint64_t t = c[p] & carry;
+                c[p] ^= carry;
+                carry = t;
             }
-            o1 = o2 = o4 = o8 = o16 = 0;
-            ng = 0;
         }
     }
     asm volatile("cp.async.wait_all;\n" ::: "memory");
+    // the thread's count: ones .. sixteens, then the 32s
+#pragma unroll
+    for (int p = kEnergyPlanes - 1; p >= 5; --p) c[p] = c[p - 5];
+    c[0] = ones;
+    c[1] = twos;
+    c[2] = fours;
+    c[3] = eights;
+    c[4] = sixteens;
     // warp sum of the bitsliced counters (at most 32 * 6 * kEnergyRun < 2^15)
     for (int o = 16; o > 0; o >>= 1) {
         uint64_t other[kEnergyPlanes];
