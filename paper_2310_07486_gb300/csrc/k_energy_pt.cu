@@ -247,6 +247,7 @@ __global__ void __launch_bounds__(64) k_pt_decide(Group g, uint32_t m, uint32_t 
 // every (w, r), walk the ladder and exchange the masked bits of positions i
 // and i+1 in the same order as the decisions.
 __global__ void k_pt_apply(Group g) {
+    constexpr int B = 8;  // slots loaded together (independent loads in flight)
     const int K = g.K;
     const size_t total = (size_t)g.W * g.R * g.N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
@@ -254,17 +255,40 @@ __global__ void k_pt_apply(Group g) {
         const size_t wr = idx / g.N, n = idx % g.N;
         const uint32_t *M = g.swapmask + wr * (K - 1) * 2;
         uint64_t *base = g.S + wr * K * (size_t)g.N + n;
+        // cur: slot i0 after the swaps of pairs < i0 (cur0: as loaded)
         uint64_t cur = base[0], cur0 = cur;
-        for (int i = 0; i + 1 < K; ++i) {
-            const uint64_t msk = (uint64_t)M[2 * i] | ((uint64_t)M[2 * i + 1] << 32);
-            uint64_t nxt = base[(size_t)(i + 1) * g.N];
-            const uint64_t nxt0 = nxt;
-            const uint64_t d = (cur ^ nxt) & msk;
-            cur ^= d;
-            nxt ^= d;
-            if (cur != cur0) base[(size_t)i * g.N] = cur;
-            cur = nxt;
-            cur0 = nxt0;
+        for (int i0 = 0; i0 + 1 < K; i0 += B) {
+            const int nb = min(B, K - 1 - i0);  // pairs i0 .. i0 + nb - 1, slots i0 + 1 .. i0 + nb
+            uint64_t msk[B];
+            uint64_t any = 0;
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                msk[k] = k < nb ? ((uint64_t)__ldg(&M[2 * (i0 + k)]) | ((uint64_t)__ldg(&M[2 * (i0 + k) + 1]) << 32)) : 0ull;
+                any |= msk[k];
+            }
+            if (!any) {
+                // no swap among these pairs: slots i0 + 1 .. i0 + nb keep their bits
+                if (cur != cur0) base[(size_t)i0 * g.N] = cur;
+                cur = cur0 = base[(size_t)(i0 + nb) * g.N];
+                continue;
+            }
+            uint64_t v[B];
+#pragma unroll
+            for (int k = 0; k < B; ++k)
+                if (k < nb) v[k] = base[(size_t)(i0 + 1 + k) * g.N];
+#pragma unroll
+            for (int k = 0; k < B; ++k) {
+                if (k < nb) {
+                    uint64_t nxt = v[k];
+                    const uint64_t nxt0 = nxt;
+                    const uint64_t d = (cur ^ nxt) & msk[k];
+                    cur ^= d;
+                    nxt ^= d;
+                    if (cur != cur0) base[(size_t)(i0 + k) * g.N] = cur;
+                    cur = nxt;
+                    cur0 = nxt0;
+                }
+            }
         }
         if (cur != cur0) base[(size_t)(K - 1) * g.N] = cur;
     }
