@@ -77,6 +77,16 @@ def _case_measure(Q, W):
     return ctx
 
 
+def _case_onetime(Q, W):
+    # L=24, L_tau=2048, 128 samples, 4 replicas, 2 k (0.15 GB): one measurement
+    # with the replica-pair and three-replica one-time sums
+    ctx = Q.Context([Q.Shape(24, 2048, 128, 4, 2, Q.HEATBATH, Q.PBC)])
+    ctx.qsg_init_samples(3, [W.uniform_ladder(0.22, 0.36, 2)])
+    ctx.qsg_sweep(2)
+    ctx.qsg_measure_correlators()
+    return ctx
+
+
 def _case_step(Q, W):
     # the bench workload (L=24, L_tau=2048, 128 samples, 4 replicas, 32 k), two
     # (sweep, tempering) rounds and one measurement: every kernel of a step once or twice
@@ -100,7 +110,8 @@ def _case_tempering(Q, W):
     return ctx
 
 
-PROFILE_CASES = {"sweep": _case_sweep, "measure": _case_measure, "step": _case_step, "tempering": _case_tempering}
+PROFILE_CASES = {"sweep": _case_sweep, "measure": _case_measure, "onetime": _case_onetime, "step": _case_step,
+                 "tempering": _case_tempering}
 
 
 def run_profile_case(name):

@@ -95,6 +95,23 @@ def test_tempering_matches_oracle(algo):
     assert ctx.qsg_read_accepts().sum() > 0
 
 
+@pytest.mark.parametrize("Ltau,boundary", [(70, Q.APBC), (130, Q.PBC), (130, Q.APBC)])
+def test_energies_with_ragged_plane_runs_match_oracle(Ltau, boundary):
+    # the energy pass takes 128-plane runs, four planes per step: L_tau = 70
+    # ends a run two planes into a step, L_tau = 130 leaves a second run of two
+    shape = Q.Shape(8, Ltau, 70, 2, 3, Q.HEATBATH, boundary)
+    lad = workloads.uniform_ladder(0.2, 0.4, 3)
+    ctx, orc = _pair(shape, lad, seed=33)
+    for _ in range(4):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    assert np.array_equal(ctx.qsg_read_accepts(), orc.accepts())
+
+
 @pytest.mark.parametrize("boundary", [Q.PBC, Q.APBC])
 def test_correlators_match_oracle(boundary):
     shape = Q.Shape(10, 40, 66, 3, 2, Q.HEATBATH, boundary)  # L^2 = 100: two x-packed words, ragged
