@@ -302,12 +302,14 @@ def test_wavefront_register_variants_match_oracle(variant, L, R, algo):
 
 
 @pytest.mark.parametrize("L,Ltau,boundary", [(10, 200, Q.APBC), (24, 130, Q.PBC), (6, 32, Q.APBC), (16, 256, Q.PBC),
-                                             (12, 384, Q.APBC), (2, 4, Q.PBC), (32, 160, Q.APBC)])
+                                             (12, 384, Q.APBC), (2, 4, Q.PBC), (32, 160, Q.APBC), (18, 96, Q.PBC),
+                                             (20, 142, Q.APBC), (26, 64, Q.APBC), (28, 48, Q.PBC)])
 def test_correlator_kernels_match_oracle(L, Ltau, boundary):
     """Tensor-core (tcgen05, FP8 +-1) and integer-pipe correlators both give the
-    oracle's int64 sums: ragged tiles (L_tau not a multiple of 128), ragged K
-    (L^2 not a multiple of 128), both boundary conditions, one and two
-    shared-memory A buffers (L = 32 leaves room for one)."""
+    oracle's int64 sums: every chunk count of the tensor-core kernel (L^2 / 128
+    rounded up: 1 .. 8), ragged tiles (L_tau not a multiple of 128; a single
+    last column block), ragged K (L^2 not a multiple of 128), both boundary
+    conditions, from three to six B stages in shared memory."""
     shape = Q.Shape(L, Ltau, 66, 2, 2, Q.HEATBATH, boundary)
     ctx, orc = _pair(shape, np.array([0.27, 0.31]), seed=55)
     ctx.qsg_sweep(3)
