@@ -360,10 +360,18 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         then on (the flag stays set for the context).  A
  *                         small value is a way to exercise that path; the
  *                         default never gives up on a working GPU.
+ *   QSG_OPT_UNITS_PER_BLOCK  work units (slot, tau chunk) per thread block of
+ *                         the generic wavefront kernel, which serves the
+ *                         lattice sizes without a compiled kernel: 0 =
+ *                         automatic (as many as fit 256 threads, at most 16),
+ *                         or 1, 2, 4, 8, 16 (rounded down to at most 512
+ *                         threads).  A unit's thread owns two site words of
+ *                         a row whatever the grouping.
  * Results do not depend on the options (except QSG_OPT_WAIT_LIMIT set too low
  * for the pipeline to make progress): every kernel produces the same bits. */
 enum { QSG_OPT_SWEEP_KERNEL = 1, QSG_OPT_CHUNK = 2, QSG_OPT_WAVEFRONT_VARIANT = 3, QSG_OPT_CORR_KERNEL = 4,
-       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7, QSG_OPT_TAIL = 8, QSG_OPT_WAIT_LIMIT = 9 };
+       QSG_OPT_PERSISTENT = 5, QSG_OPT_GRAPH = 6, QSG_OPT_ONETIME = 7, QSG_OPT_TAIL = 8, QSG_OPT_WAIT_LIMIT = 9,
+       QSG_OPT_UNITS_PER_BLOCK = 10 };
 qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value);
 
 /* Sweeps without any device allocation.  (This entry point has no

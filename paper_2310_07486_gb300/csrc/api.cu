@@ -208,6 +208,7 @@ struct qsg_ctx {
     int persistent = 0;    // QSG_OPT_PERSISTENT: 0 automatic, 1 off, 2 persistent kernel, 3 one stream per group
     int triples = 1;       // QSG_OPT_ONETIME: 1 with the three-replica sums, 0 without
     int tail = 0;          // QSG_OPT_TAIL: slots swept in quarter-length chunks, last
+    int upb = 0;           // QSG_OPT_UNITS_PER_BLOCK: 0 automatic, else 1, 2, 4, 8 or 16
     unsigned wait_limit = kDefaultWaitLimit;  // QSG_OPT_WAIT_LIMIT: polls per bounded device wait
     PlanBuffers pb;
     PersistentPlan plan{};
@@ -503,8 +504,8 @@ static qsg_status launch_one_sweep(qsg_ctx *ctx, bool persistent, const uint32_t
 
 // (Re)capture the graph of graph_batch sweeps when a launch option changed.
 static qsg_status ensure_graph(qsg_ctx *ctx, SweepMode mode) {
-    const long long key = (((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 4 + (int)mode) * 4 +
-                            g_wavefront_variant) * 65537LL + ctx->chunk) * 65537LL + ctx->tail;
+    const long long key = ((((((long long)ctx->graph_batch * 4 + ctx->sweep_kernel) * 4 + (int)mode) * 4 +
+                             g_wavefront_variant) * 65537LL + ctx->chunk) * 65537LL + ctx->tail) * 32 + ctx->upb;
     if (ctx->graph_exec && ctx->graph_key == key) return QSG_OK;
     if (ctx->graph_exec) {
         cudaGraphExecDestroy(ctx->graph_exec);
@@ -832,6 +833,12 @@ qsg_status qsg_set_option(qsg_ctx *ctx, int32_t option, int64_t value) {
     if (option == QSG_OPT_TAIL) {
         if (value < 0 || value > (1 << 24)) return QSG_ERR_ARG;
         ctx->tail = (int)value;
+        return QSG_OK;
+    }
+    if (option == QSG_OPT_UNITS_PER_BLOCK) {
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16) return QSG_ERR_ARG;
+        ctx->upb = (int)value;
+        for (Group &g : ctx->groups) g.upb = ctx->upb;
         return QSG_OK;
     }
     if (option == QSG_OPT_WAIT_LIMIT) {

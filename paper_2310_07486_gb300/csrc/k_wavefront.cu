@@ -405,9 +405,16 @@ int wavefront_chunk(const Group &g, int requested) {
 
 int g_wavefront_variant = 0;  // see launch_sweep_wavefront
 
+// Work units per block: g.upb rounded down to a power of two with at most 512
+// threads, or by default the most that fit 256 threads (up to 16).  Units are
+// independent, so the grouping changes no bit.
 int wavefront_units_per_block(const Group &g) {
     const int tpu = g.L * g.L / 2;
     int P = 1;
+    if (g.upb > 0) {
+        while (P * 2 <= g.upb && P * 2 <= 16 && (P * 2) * tpu <= 512) P *= 2;
+        return P;
+    }
     while ((P * 2) * tpu <= 256 && P * 2 <= 16) P *= 2;
     return P;
 }

@@ -40,6 +40,7 @@ struct Group {
     double *wcos;             // [L/2+1] cos(2 pi d / L), host FP64
     double xi_norm;           // 2 sin(pi / L), host FP64
     unsigned *arrivals;  // [nslots][L_tau/4] boundary arrival counters of the wavefront sweep
+    int upb;             // work units per block of the generic wavefront kernel (0 = automatic)
 };
 
 // ---------------------------------------------------------------------------

@@ -22,6 +22,7 @@ PBC, APBC = 0, 1
 OPT_SWEEP_KERNEL, OPT_CHUNK, OPT_WAVEFRONT_VARIANT, OPT_CORR_KERNEL, OPT_PERSISTENT, OPT_GRAPH, OPT_ONETIME, OPT_TAIL = \
     1, 2, 3, 4, 5, 6, 7, 8
 OPT_WAIT_LIMIT = 9
+OPT_UNITS_PER_BLOCK = 10
 CORR_TENSOR, CORR_INTEGER = 0, 1
 SWEEP_AUTO, SWEEP_REFERENCE, SWEEP_WAVEFRONT = 0, 1, 2
 

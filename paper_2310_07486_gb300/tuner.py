@@ -1,14 +1,15 @@
 """Launch-option autotuner for qsg_sweep.
 
 Every option of ``qsg_set_option`` that shapes the sweep launch (tau chunk per
-work unit, kernel form, persistent multi-group launch, CUDA-graph batch,
-slots swept in shorter chunks at the end of a launch) leaves the sampled bits
-unchanged, so the choice is purely one of speed.  The tuner times each valid
-combination of the first four on the caller's own context with CUDA events on
-the context's stream, then the tail lengths with the best launch of each of the
-four fastest chunk lengths, keeps the
-fastest, and caches the choice in a JSON file keyed by the group shapes, the
-device name and the library build.
+work unit, kernel form, persistent multi-group launch, CUDA-graph batch, work
+units per block of the generic kernel, slots swept in shorter chunks at the
+end of a launch) leaves the sampled bits unchanged, so the choice is purely
+one of speed.  The tuner times each valid combination of the first four on the
+caller's own context with CUDA events on the context's stream, then (when a
+group runs the generic kernel) the units per block, then the tail lengths with
+the best launch of each of the four fastest chunk lengths, keeps the fastest,
+and caches the choice in a JSON file keyed by the group shapes, the device
+name and the library build.
 
 Tuning runs real sweeps, so the spins and counters of every group are saved
 to the host first and put back afterwards: a tuned run samples exactly what an
@@ -28,8 +29,10 @@ DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build
 
 # option id -> name used in the cache and in reports
 _NAMES = {Q.OPT_CHUNK: "chunk", Q.OPT_WAVEFRONT_VARIANT: "variant", Q.OPT_PERSISTENT: "persistent",
-          Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail"}
-DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0}
+          Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail", Q.OPT_UNITS_PER_BLOCK: "upb"}
+DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0, "upb": 0}
+UPB = [1, 2, 4, 8, 16]  # units per block of the generic kernel, tried after the first stage
+COMPILED_L = (20, 24)   # lattice sizes with a compiled one-unit-per-block kernel
 TAILS = [0, 16, 24, 28, 32, 40, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
 VARIANTS = [0, 1, 2, 3]  # forms of the wavefront kernel (QSG_OPT_WAVEFRONT_VARIANT)
 
@@ -60,8 +63,9 @@ def candidate_chunks(shapes, largest=512):
 
 
 def candidates(shapes, sweeps_per_call, space=None):
-    """Launch options to time; `space` may restrict any of "chunk",
-    "variant", "persistent", "graph" to a list of values."""
+    """Launch options of the first stage; `space` may restrict any of
+    "chunk", "variant", "persistent", "graph" (and "upb", the later stage's
+    units per block) to a list of values."""
     space = space or {}
     chunks = [c for c in candidate_chunks(shapes) if c in space.get("chunk", [c])]
     persistent = [1, 2, 3] if len(shapes) > 1 else [1]
@@ -70,7 +74,13 @@ def candidates(shapes, sweeps_per_call, space=None):
     graph = [g for g in graph if g in space.get("graph", [g])]
     variants = [v for v in VARIANTS if v in space.get("variant", [v])]
     for chunk, variant, pers, gr in itertools.product(chunks, variants, persistent, graph):
-        yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0}
+        yield {"chunk": chunk, "variant": variant, "persistent": pers, "graph": gr, "tail": 0, "upb": 0}
+
+
+def uses_generic_kernel(shapes, variant):
+    """True if some group is swept by the generic wavefront kernel (a lattice
+    size without a compiled kernel, or the generic form asked for)."""
+    return variant == 2 or any(s.L not in COMPILED_L for s in shapes)
 
 
 def apply(ctx, choice: dict) -> None:
@@ -80,6 +90,7 @@ def apply(ctx, choice: dict) -> None:
     ctx.qsg_set_option(Q.OPT_WAVEFRONT_VARIANT, int(choice["variant"]))
     ctx.qsg_set_option(Q.OPT_PERSISTENT, int(choice["persistent"]))
     ctx.qsg_set_option(Q.OPT_TAIL, int(choice.get("tail", 0)))
+    ctx.qsg_set_option(Q.OPT_UNITS_PER_BLOCK, int(choice.get("upb", 0)))
     ctx.qsg_set_option(Q.OPT_GRAPH, int(choice["graph"]))
 
 
@@ -136,9 +147,22 @@ def tune(ctx, sweeps_per_call=10, reps=3, cache_path=DEFAULT_CACHE, use_cache=Tr
             table.append((t, cand))
             if verbose:
                 print(f"  {cand} {t:.4f} ms/sweep", flush=True)
-        # second stage: the tail lengths with the best launch of each chunk
-        # length (a longer chunk that fills the last wave badly without a tail
-        # can win with one)
+        # units per block of the generic kernel, with the best launch so far
+        if table:
+            t0, first = min(table, key=lambda tc: tc[0])
+            if uses_generic_kernel(ctx.shapes, first["variant"]):
+                for upb in [u for u in UPB if u in (space or {}).get("upb", UPB)]:
+                    cand = dict(first, upb=upb)
+                    try:
+                        apply(ctx, cand)
+                    except Q.QSGError:
+                        continue
+                    t = _time_call(ctx, sweeps_per_call, reps)
+                    table.append((t, cand))
+                    if verbose:
+                        print(f"  {cand} {t:.4f} ms/sweep", flush=True)
+        # the tail lengths with the best launch of each chunk length (a longer
+        # chunk that fills the last wave badly without a tail can win with one)
         best_per_chunk = {}
         for t, cand in table:
             c = cand["chunk"]

@@ -269,6 +269,33 @@ def test_wavefront_sweep_matches_oracle(L, Ltau, chunk, algo, boundary):
     assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
 
 
+@pytest.mark.parametrize("L,upb", [(8, 1), (8, 2), (8, 4), (8, 16), (12, 2), (16, 4), (4, 16)])
+def test_units_per_block_of_the_generic_kernel_match_oracle(L, upb):
+    """Grouping work units into blocks (QSG_OPT_UNITS_PER_BLOCK) changes no
+    bit: every grouping, including ones rounded down to 512 threads, gives the
+    oracle's spins; values that are not 0 or a power of two up to 16 are
+    rejected."""
+    shape = Q.Shape(L, 64, 70, 2, 3, Q.METROPOLIS, Q.APBC)
+    ctx, orc = _pair(shape, workloads.uniform_ladder(0.22, 0.34, 3), seed=44)
+    for bad in (-1, 3, 32):
+        with pytest.raises(Q.QSGError):
+            ctx.qsg_set_option(Q.OPT_UNITS_PER_BLOCK, bad)
+    ctx.qsg_set_option(Q.OPT_SWEEP_KERNEL, Q.SWEEP_WAVEFRONT)
+    ctx.qsg_set_option(Q.OPT_CHUNK, 16)
+    ctx.qsg_set_option(Q.OPT_UNITS_PER_BLOCK, upb)
+    for _ in range(2):
+        ctx.qsg_sweep(3)
+        orc.sweep(3)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    # and inside a captured graph
+    ctx.qsg_set_option(Q.OPT_GRAPH, 4)
+    ctx.qsg_sweep(4)
+    orc.sweep(4)
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+
+
 def test_reference_and_wavefront_kernels_agree_at_mid_scale():
     w = workloads.mid_scale()
     out = []
