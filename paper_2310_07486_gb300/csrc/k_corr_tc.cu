@@ -376,10 +376,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp < kProducerWarps) {
         // ------------------------------------------------------------ producers
         // the bit words of the next block are loaded into registers while the
-        // current one is expanded; one chunk loop serves both kinds of block
-        // (one inline expansion per chunk keeps the code small): an A block's
-        // thread writes word tid >> 7 of row tid & 127, a pair block's thread
-        // both words of stage row tid (none past a single last block)
+        // current one is expanded; one chunk loop serves both kinds of block:
+        // an A block's thread writes word tid >> 7 of row tid & 127, a pair
+        // block's thread both words of stage row tid (none past a single
+        // last block)
         Seq cur, nxt;
         cur.u = blockIdx.x;
         seq_unit(cur, nunits, nhalf);
@@ -398,13 +398,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int row = isA ? (tid & 127) : tid, hh0 = isA ? (tid >> 7) : 0;
             const int nw = isA ? 1 : ((pair || tid < kTile) ? 2 : 0);
             const int t = isA ? cur.i * kTile + row : (cur.jp + (tid >> 7)) * kTile + (tid & 127);
-#pragma unroll
+            // the chunk loop stays rolled (the three roles' code shares the
+            // instruction cache): the words of chunk kc are always in wc[0],
+            // wc[1] (an A block's in wc[0]), and the array shifts after a chunk
+#pragma unroll 1
             for (int kc = 0; kc < NC; ++kc) {
                 const bool ok = isA ? mbar_wait(&ctl.aempty[kc], a_ph, &ctl.abort, wait_limit)
                                     : mbar_wait(&ctl.bempty[s], b_par, &ctl.abort, wait_limit);
                 uint8_t *rowp = isA ? sA + (size_t)kc * kChunkBytes + row * kChunk
                                     : sB + (size_t)s * kStageBytes + row * kChunk;
-                const uint64_t w0 = isA ? wc[kc] : wc[2 * kc], w1 = wc[2 * kc + 1];
+                const uint64_t w0 = wc[0], w1 = wc[1];
                 if (ok) {
 #pragma unroll 1
                     for (int k = 0; k < nw; ++k) {
@@ -419,6 +422,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     s = 0;
                     b_par ^= 1u;
                 }
+                const int sh = isA ? 1 : 2;  // words per chunk of this kind of block
+#pragma unroll
+                for (int k = 0; k < 2 * NC - 2; ++k) wc[k] = sh == 1 ? wc[k + 1] : wc[k + 2];
             }
             if (isA) a_ph ^= 1u;
 #pragma unroll
@@ -508,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bool ok = mbar_wait(&ctl.accempty[a], ((n_t >> 1) & 1u) ^ 1u, &ctl.abort, wait_limit);
                         asm volatile("tcgen05.fence::after_thread_sync;\n");
                         const uint32_t d = tmem + (uint32_t)(a * 256);
-#pragma unroll
+#pragma unroll 1  // rolled: the three roles' code shares the instruction cache
                         for (int kc = 0; kc < NC; ++kc) {
                             ok = mbar_wait(&ctl.afull[kc], a_par, &ctl.abort, wait_limit) && ok;
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
@@ -532,7 +538,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         asm volatile("tcgen05.fence::after_thread_sync;\n");
                         const uint32_t d = tmem + (uint32_t)(a * 256);
                         const uint32_t idesc = pair ? id256 : id128;
-#pragma unroll
+#pragma unroll 1  // rolled: the three roles' code shares the instruction cache
                         for (int kc = 0; kc < NC; ++kc) {
                             ok = mbar_wait(&ctl.bfull[bs], b_par, &ctl.abort, wait_limit) && ok;
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
