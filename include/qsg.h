@@ -148,6 +148,25 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx);
  * C_acc then Q_acc then P_acc in the same layouts.  Synchronises the stream. */
 qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw);
 
+/* qsg_read_correlators without the host wait: the finish runs on the
+ * context's stream and the copies (same outputs and layouts) on copy_stream
+ * (a cudaStream_t other than the context's), which waits for the finish.  The
+ * call returns once the work is queued; the host buffers (page-locked for the
+ * copies to overlap compute) hold the results once qsg_wait_correlators
+ * returns or copy_stream has been synchronised, and must stay allocated until
+ * then.  Every later call of the context that writes the correlator buffers
+ * (qsg_measure_correlators, a read, qsg_init_samples) is ordered after the
+ * copies on the device, so the caller may go on measuring at once.  The
+ * device flag is copied with the results and reported by
+ * qsg_wait_correlators.  QSG_ERR_ARG for a NULL or the context's own stream. */
+qsg_status qsg_read_correlators_async(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw,
+                                      void *copy_stream);
+
+/* Blocks until the copies of the last qsg_read_correlators_async are done.
+ * QSG_ERR_TIMEOUT if the device flag was set by then (as qsg_read_correlators
+ * reports it), QSG_OK otherwise or when no asynchronous read is pending. */
+qsg_status qsg_wait_correlators(qsg_ctx *ctx);
+
 /* One-time observables of one group (Methods, "One-time observables";
  * Eqs. (chi-r), (xi-r), (Binder)) and the linear susceptibility (Sect. "On the
  * magnetic susceptibilities"), finished in FP64 on the device from the sums

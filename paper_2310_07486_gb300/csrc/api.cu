@@ -228,7 +228,19 @@ struct qsg_ctx {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
+    // qsg_read_correlators_async: the finish's completion on `stream` and the
+    // completion of the copies on the caller's stream, which every later
+    // writer of the correlator buffers waits for
+    cudaEvent_t fin_ev = nullptr, copy_ev = nullptr;
+    bool copy_pending = false;
+    int *h_flag = nullptr;  // page-locked copy of the device flag, taken with the copies
+    bool flag_pending = false;
     ~qsg_ctx() {
+        // the copies read the workspace, which the caller frees after this
+        if (copy_pending) cudaEventSynchronize(copy_ev);
+        if (fin_ev) cudaEventDestroy(fin_ev);
+        if (copy_ev) cudaEventDestroy(copy_ev);
+        if (h_flag) cudaFreeHost(h_flag);
         if (graph_exec) cudaGraphExecDestroy(graph_exec);
         if (cap_stream) cudaStreamDestroy(cap_stream);
         for (cudaStream_t t : side) cudaStreamDestroy(t);
@@ -248,6 +260,16 @@ static qsg_status cuda_fail(qsg_ctx *c, cudaError_t e) {
         cudaError_t _e = (expr);                           \
         if (_e != cudaSuccess) return cuda_fail((c), _e);  \
     } while (0)
+
+// Order the context's stream after the correlator copies of the last
+// qsg_read_correlators_async (they read buffers the next finish, measurement
+// or initialisation writes).
+static qsg_status order_after_copies(qsg_ctx *c) {
+    if (!c->copy_pending) return QSG_OK;
+    QSG_CUDA(c, cudaStreamWaitEvent(c->stream, c->copy_ev, 0));
+    c->copy_pending = false;
+    return QSG_OK;
+}
 
 static qsg_status check_device_flag(qsg_ctx *c) {
     int h = 0;
@@ -373,6 +395,7 @@ qsg_status qsg_init_samples(qsg_ctx *ctx, uint64_t seed, const double *k_ladders
         lad += g.K;
     }
     ctx->seed = seed;
+    if (qsg_status o = order_after_copies(ctx)) return o;
     cudaStream_t st = ctx->stream;
     for (size_t gi = 0; gi < ctx->groups.size(); ++gi) {
         const Group &g = ctx->groups[gi];
@@ -590,6 +613,7 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
     Range range("qsg_measure_correlators");
     if (!ctx) return QSG_ERR_ARG;
     if (!ctx->initialised) return QSG_ERR_STATE;
+    if (qsg_status o = order_after_copies(ctx)) return o;
     for (const Group &g : ctx->groups)
         QSG_CUDA(ctx, launch_measure(g, ctx->scratch, ctx->scratch_words, ctx->corr_tensor, ctx->triples, ctx->d_err,
                                      ctx->wait_limit, ctx->stream));
@@ -597,12 +621,9 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx) {
     return QSG_OK;
 }
 
-qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw) {
-    Range range("qsg_read_correlators");
-    if (!ctx || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
-    if (!ctx->initialised) return QSG_ERR_STATE;
-    const Group &g = ctx->groups[group];
-    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
+// The copies of qsg_read_correlators on stream st.
+static qsg_status copy_correlators(qsg_ctx *ctx, const Group &g, double *C, double *Q2, double *q2, int64_t *raw,
+                                   cudaStream_t st) {
     // device layout [R][W*64][K][nl]; the host keeps the first n_samples of the
     // W*64 sample bits, so every replica is one contiguous block on both sides
     // and the copies go straight into the caller's buffers (at DMA speed when
@@ -611,24 +632,63 @@ qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *
     const size_t blk = (size_t)S * K * nl, pitch = (size_t)Sp * K * nl, outc = (size_t)g.R * blk;
     for (int r = 0; r < g.R; ++r) {
         if (C)
-            QSG_CUDA(ctx, cudaMemcpyAsync(C + r * blk, g.outC + r * pitch, sizeof(double) * blk, cudaMemcpyDeviceToHost,
-                                          ctx->stream));
+            QSG_CUDA(ctx, cudaMemcpyAsync(C + r * blk, g.outC + r * pitch, sizeof(double) * blk, cudaMemcpyDeviceToHost, st));
         if (Q2)
-            QSG_CUDA(ctx, cudaMemcpyAsync(Q2 + r * blk, g.outQ + r * pitch, sizeof(double) * blk,
-                                          cudaMemcpyDeviceToHost, ctx->stream));
+            QSG_CUDA(ctx, cudaMemcpyAsync(Q2 + r * blk, g.outQ + r * pitch, sizeof(double) * blk, cudaMemcpyDeviceToHost, st));
         if (raw) {
             QSG_CUDA(ctx, cudaMemcpyAsync(raw + r * blk, g.Cacc + r * pitch, sizeof(long long) * blk,
-                                          cudaMemcpyDeviceToHost, ctx->stream));
+                                          cudaMemcpyDeviceToHost, st));
             QSG_CUDA(ctx, cudaMemcpyAsync(raw + outc + r * blk, g.Qacc + r * pitch, sizeof(long long) * blk,
-                                          cudaMemcpyDeviceToHost, ctx->stream));
+                                          cudaMemcpyDeviceToHost, st));
         }
     }
-    if (q2)
-        QSG_CUDA(ctx, cudaMemcpyAsync(q2, g.outP, sizeof(double) * (size_t)S * K, cudaMemcpyDeviceToHost, ctx->stream));
+    if (q2) QSG_CUDA(ctx, cudaMemcpyAsync(q2, g.outP, sizeof(double) * (size_t)S * K, cudaMemcpyDeviceToHost, st));
     if (raw)
         QSG_CUDA(ctx, cudaMemcpyAsync(raw + 2 * outc, g.Pacc, sizeof(long long) * (size_t)S * K, cudaMemcpyDeviceToHost,
-                                      ctx->stream));
+                                      st));
+    return QSG_OK;
+}
+
+qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw) {
+    Range range("qsg_read_correlators");
+    if (!ctx || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    if (qsg_status o = order_after_copies(ctx)) return o;
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
+    if (qsg_status o = copy_correlators(ctx, g, C, Q2, q2, raw, ctx->stream)) return o;
     return check_device_flag(ctx);
+}
+
+qsg_status qsg_read_correlators_async(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw,
+                                      void *copy_stream) {
+    Range range("qsg_read_correlators_async");
+    if (!ctx || !copy_stream || group < 0 || group >= (int)ctx->groups.size()) return QSG_ERR_ARG;
+    if (!ctx->initialised) return QSG_ERR_STATE;
+    cudaStream_t cs = static_cast<cudaStream_t>(copy_stream);
+    if (cs == ctx->stream) return QSG_ERR_ARG;
+    if (qsg_status o = order_after_copies(ctx)) return o;
+    if (!ctx->fin_ev) QSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->fin_ev, cudaEventDisableTiming));
+    if (!ctx->copy_ev) QSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
+    if (!ctx->h_flag) QSG_CUDA(ctx, cudaHostAlloc((void **)&ctx->h_flag, sizeof(int), cudaHostAllocDefault));
+    const Group &g = ctx->groups[group];
+    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
+    QSG_CUDA(ctx, cudaEventRecord(ctx->fin_ev, ctx->stream));
+    QSG_CUDA(ctx, cudaStreamWaitEvent(cs, ctx->fin_ev, 0));
+    if (qsg_status o = copy_correlators(ctx, g, C, Q2, q2, raw, cs)) return o;
+    QSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, cs));
+    QSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, cs));
+    ctx->copy_pending = true;
+    ctx->flag_pending = true;
+    return QSG_OK;
+}
+
+qsg_status qsg_wait_correlators(qsg_ctx *ctx) {
+    if (!ctx) return QSG_ERR_ARG;
+    if (!ctx->flag_pending) return QSG_OK;
+    QSG_CUDA(ctx, cudaEventSynchronize(ctx->copy_ev));
+    ctx->flag_pending = false;
+    return *ctx->h_flag == DEVERR_NONE ? QSG_OK : QSG_ERR_TIMEOUT;
 }
 
 qsg_status qsg_read_onetime(qsg_ctx *ctx, int32_t group, double *per_sample, double *per_k, int64_t *raw) {

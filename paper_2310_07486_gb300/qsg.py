@@ -73,6 +73,10 @@ def load_library(path: str | None = None):
     lib.qsg_measure_correlators.argtypes = [vp]
     lib.qsg_read_correlators.restype = i32
     lib.qsg_read_correlators.argtypes = [vp, i32, vp, vp, vp, vp]
+    lib.qsg_read_correlators_async.restype = i32
+    lib.qsg_read_correlators_async.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    lib.qsg_wait_correlators.restype = i32
+    lib.qsg_wait_correlators.argtypes = [vp]
     lib.qsg_read_energies.restype = i32
     lib.qsg_read_onetime.argtypes = [vp, i32, vp, vp, vp]
     lib.qsg_read_onetime.restype = i32
@@ -137,7 +141,7 @@ def load_library(path: str | None = None):
 def exported_symbols():
     return ["qsg_workspace_bytes", "qsg_create", "qsg_destroy", "qsg_set_stream", "qsg_init_samples",
             "qsg_set_couplings", "qsg_sweep", "qsg_tempering_swap", "qsg_measure_correlators",
-            "qsg_read_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
+            "qsg_read_correlators", "qsg_read_correlators_async", "qsg_wait_correlators", "qsg_read_energies", "qsg_read_accepts", "qsg_get_spins", "qsg_set_spins",
             "qsg_get_spins_device", "qsg_set_spins_device",
             "qsg_get_counters", "qsg_set_counters", "qsg_set_option", "qsg_sweep_static_scratch", "qsg_kernel_launches", "qsg_strerror", "qsg_last_cuda_error"]
 
@@ -321,6 +325,33 @@ class Context:
             out.update(C_raw=R[:nc].reshape(shp), Q2_raw=R[nc:2 * nc].reshape(shp),
                        q2_raw=R[2 * nc:].reshape(s.n_samples, s.n_k))
         return out
+
+    def qsg_read_correlators_async(self, out, stream, group=0):
+        """Queues the finish of one group on the context's stream and the
+        copies into `out` (from correlator_buffers, pinned for overlap) on
+        `stream` (a torch.cuda.Stream or a raw cudaStream_t other than the
+        context's); returns at once.  `out` holds the results after
+        qsg_wait_correlators(); this object keeps it referenced until then."""
+        s = self.shapes[group]
+        shp = (s.n_replicas, s.n_samples, s.n_k, s.n_lag)
+        C, Q, P = out["C"], out["Q2"], out["q2"]
+        for a, want in ((C, shp), (Q, shp), (P, (s.n_samples, s.n_k))):
+            if a.shape != want or a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError("qsg_read_correlators_async: out arrays must be C-contiguous float64 of shape %s"
+                                 % (want,))
+        raw_stream = getattr(stream, "cuda_stream", stream)
+        self._check(self.lib.qsg_read_correlators_async(self.h, group, _ptr(C), _ptr(Q), _ptr(P), None,
+                                                        ctypes.c_void_p(int(raw_stream))),
+                    "qsg_read_correlators_async")
+        self._pending_out = getattr(self, "_pending_out", []) + [out]
+
+    def qsg_wait_correlators(self):
+        """Waits for the copies of the last qsg_read_correlators_async;
+        raises on the device flag as qsg_read_correlators does."""
+        try:
+            self._check(self.lib.qsg_wait_correlators(self.h), "qsg_wait_correlators")
+        finally:
+            self._pending_out = []
 
     ONETIME_SAMPLE_FIELDS = ("q2", "q4", "chi2", "F2", "chi3", "F3", "chi_lin")
     ONETIME_K_FIELDS = ("chi2", "F2", "xi2", "chi3", "F3", "xi3", "B", "chi_lin")

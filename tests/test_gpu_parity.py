@@ -549,6 +549,41 @@ def test_correlator_readback_into_caller_buffers(pinned):
         assert np.array_equal(got[k], ref[k])
 
 
+def test_asynchronous_readback_is_ordered_before_the_next_measurement():
+    """qsg_read_correlators_async queues the finish and copies and returns;
+    a measurement and a second asynchronous read issued right after it must
+    not overwrite the first read's sources before they are copied.  Both
+    reads match the oracle after their own measurement, and a NULL copy
+    stream is refused."""
+    import torch
+    shape = Q.Shape(6, 32, 70, 3, 2, Q.HEATBATH, Q.APBC)
+    ctx, orc = _pair(shape, np.array([0.27, 0.31]), seed=13)
+    copy_stream = torch.cuda.Stream()
+    with pytest.raises(Q.QSGError):
+        ctx.qsg_read_correlators_async(ctx.correlator_buffers(), 0)
+    outs, refs = [], []
+    for rep in range(2):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_measure_correlators()
+        orc.measure()
+        refs.append(orc.read())
+        out = ctx.correlator_buffers(pinned=True)
+        for a in out.values():
+            a.fill(np.nan)
+        ctx.qsg_read_correlators_async(out, copy_stream)
+        outs.append(out)
+    ctx.qsg_wait_correlators()
+    for out, ref in zip(outs, refs):
+        for k in ("C", "Q2", "q2"):
+            a, b = out[k], ref[k]
+            both_nan = np.isnan(a) & np.isnan(b)
+            assert np.all(both_nan | (np.abs(a - b) <= RTOL * np.maximum(np.abs(b), 1e-300))), k
+    # the synchronous read after the asynchronous ones still agrees
+    _check_corr(ctx.qsg_read_correlators(raw=True), refs[-1])
+    ctx.qsg_wait_correlators()  # nothing pending: returns at once
+
+
 @pytest.mark.parametrize("Ltau,chunk,tail", [(128, 64, 3), (128, 128, 12), (128, 64, 100), (1024, 512, 5)])
 def test_wavefront_tail_slots_in_short_chunks_match_oracle(Ltau, chunk, tail):
     """The last `tail` slots swept in quarter-length chunks after every other
