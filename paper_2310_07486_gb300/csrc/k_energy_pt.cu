@@ -181,21 +181,246 @@ __global__ void __launch_bounds__(512, 2) k_energy(Group g) {
         if (cnt[b]) atomicAdd(&g.U[(size_t)s * 64 + b], cnt[b]);
 }
 
-cudaError_t launch_energy(const Group &g, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(g.U, 0, sizeof(int32_t) * (size_t)g.nslots * 64, st);
-    if (e != cudaSuccess) return e;
+// k_energy with L compiled in (the lattice sizes of the sweep's fixed-L
+// kernels and the smaller even sizes of the ragged workloads).  The same
+// count, in a leaner loop: each step's four planes come in one cp.async group
+// and the four refill copies use constant offsets; a thread keeps its own two
+// words of the next plane (they are the +tau neighbours of this one) in
+// registers, so a plane costs three shared-memory loads; only a step that
+// runs past the block's last plane takes the per-plane checks; every plane
+// index of the ring is fixed by the step's first plane.
+template <int L>
+__host__ __device__ constexpr int energy_threads() {
+    return (L * L / 2 + 31) / 32 * 32;
+}
+
+template <int L, int RUN>
+__global__ void __launch_bounds__(energy_threads<L>(), 3) k_energy_l(Group g) {
+    constexpr int L2 = L * L;
+    constexpr int kT = energy_threads<L>();
+    constexpr int kThirty = RUN <= 128 ? 5 : 6;            // planes of the count of 32s (6 RUN / 32 < 2^kThirty)
+    constexpr int kPlanes = RUN <= 128 ? 15 : 16;          // bits of a warp's count (32 x 6 x RUN < 2^kPlanes)
+    static_assert(RUN % 4 == 0 && RUN <= 256, "run of planes");
+    extern __shared__ __align__(16) uint64_t ring[];       // [kEnergyBuf][L2]
+    __shared__ int cnt[64];
+    const int s = blockIdx.x;
+    const int Lt = g.Ltau;
+    const int t0 = blockIdx.y * RUN, t1 = min(t0 + RUN, Lt);
+    const int tid = threadIdx.x;
+    for (int b = tid; b < 64; b += kT) cnt[b] = 0;
+    const int xy = 2 * tid;
+    const bool own = xy < L2;  // sites xy and xy + 1 (L is even: one row)
+    const int y = xy / L, x = xy - (xy / L) * L;
+    const int xr = y * L + (x + 2 == L ? 0 : x + 2);      // right neighbour of site xy + 1
+    const int yu = (y + 1 == L ? 0 : y + 1) * L + x;       // up neighbours: yu, yu + 1
+    const int w = s / (g.R * g.K);
+    const uint64_t *Sx = g.S + (size_t)s * g.N + xy;       // the thread's column of words
+    const unsigned ring0 = (unsigned)__cvta_generic_to_shared(ring) + 8u * (unsigned)xy;
+    uint64_t j0x = 0, j1x = 0, j0y = 0, j1y = 0;
+    if (own) {
+        j0x = g.Jx[(size_t)w * L2 + xy];
+        j1x = g.Jx[(size_t)w * L2 + xy + 1];
+        j0y = g.Jy[(size_t)w * L2 + xy];
+        j1y = g.Jy[(size_t)w * L2 + xy + 1];
+    }
+    const uint64_t apbc = g.boundary == 1 ? ~0ull : 0ull;
+    auto copy = [&](int q, int gq) {
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(ring0 + 8u * (unsigned)((q % kEnergyBuf) * L2)),
+                     "l"(Sx + (size_t)gq * L2)
+                     : "memory");
+    };
+    // planes q .. q + 3 (those up to t1; plane Lt is plane 0) as one group
+    auto issue4 = [&](int q) {
+        if (own) {
+            if (q + 3 <= t1 && q + 3 < Lt) {
+                const unsigned d = ring0 + 8u * (unsigned)((q % kEnergyBuf) * L2);
+                const uint64_t *src = Sx + (size_t)q * L2;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + 8u * i * L2), "l"(src + i * L2)
+                                 : "memory");
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (q + i <= t1) copy(q + i, q + i == Lt ? 0 : q + i);
+            }
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    issue4(t0);
+    issue4(t0 + 4);
+    issue4(t0 + 8);
+    uint64_t ones = 0, twos = 0, fours = 0, eights = 0, sixteens = 0;
+    uint64_t c32[kThirty];
+#pragma unroll
+    for (int p = 0; p < kThirty; ++p) c32[p] = 0;
+    ulonglong2 v = make_ulonglong2(0ull, 0ull);  // the thread's words of the current plane
+    // the six bond words of plane P (next plane Pn); v moves on to the next plane
+    auto bonds = [&](const uint64_t *P, const uint64_t *Pn, uint64_t ft, uint64_t (&b)[6]) {
+        const ulonglong2 u = *reinterpret_cast<const ulonglong2 *>(P + yu);
+        const uint64_t r1 = P[xr];
+        const ulonglong2 n = *reinterpret_cast<const ulonglong2 *>(Pn + xy);
+        b[0] = v.x ^ v.y ^ j0x;
+        b[1] = v.x ^ u.x ^ j0y;
+        b[2] = v.x ^ n.x ^ ft;
+        b[3] = v.y ^ r1 ^ j1x;
+        b[4] = v.y ^ u.y ^ j1y;
+        b[5] = v.y ^ n.y ^ ft;
+        v = n;
+    };
+    auto tree12 = [&](const uint64_t (&a)[6], const uint64_t (&b)[6], uint64_t &eA, uint64_t &eB) {
+        uint64_t tA, tB, tC, tD, tE, tF, fA, fB, fC;
+        csa(tA, ones, ones, a[0], a[1]);
+        csa(tB, ones, ones, a[2], a[3]);
+        csa(fA, twos, twos, tA, tB);
+        csa(tC, ones, ones, a[4], a[5]);
+        csa(tD, ones, ones, b[0], b[1]);
+        csa(fB, twos, twos, tC, tD);
+        csa(eA, fours, fours, fA, fB);
+        csa(tE, ones, ones, b[2], b[3]);
+        csa(tF, ones, ones, b[4], b[5]);
+        csa(fC, twos, twos, tE, tF);
+        eB = fours & fC;
+        fours ^= fC;
+    };
+    auto ripple = [&](uint64_t carry) {  // count of 32s += carry
+#pragma unroll
+        for (int p = 0; p < kThirty; ++p) {
+            const uint64_t t = c32[p] & carry;
+            c32[p] ^= carry;
+            carry = t;
+        }
+    };
+    int q = t0;
+    for (; q + 4 <= t1; q += 4) {
+        // planes q .. q + 4 have landed (the group of q + 8 .. q + 11 may be in flight)
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        __syncthreads();
+        // the slots of planes q - 4 .. q - 1 are free for every thread: refill them
+        issue4(q + 12);
+        if (own) {
+            const uint64_t *P = ring + (q % kEnergyBuf) * L2;
+            if (q == t0) v = *reinterpret_cast<const ulonglong2 *>(P + xy);
+            // only the last of the four planes can close the tau ring
+            const uint64_t ft3 = q + 4 == Lt ? apbc : 0ull;
+            uint64_t a[6], b[6], eA1, eB1, eA2, eB2;
+            bonds(P, P + L2, 0ull, a);
+            bonds(P + L2, P + 2 * L2, 0ull, b);
+            tree12(a, b, eA1, eB1);
+            bonds(P + 2 * L2, P + 3 * L2, 0ull, a);
+            bonds(P + 3 * L2, ring + ((q + 4) % kEnergyBuf) * L2, ft3, b);
+            tree12(a, b, eA2, eB2);
+            uint64_t s16a, s16b, carry;
+            csa(s16a, eights, eights, eA1, eB1);
+            csa(s16b, eights, eights, eA2, eB2);
+            csa(carry, sixteens, sixteens, s16a, s16b);
+            ripple(carry);
+        }
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (q < t1) {
+        // two planes left (runs and L_tau are even)
+        __syncthreads();
+        if (own) {
+            const uint64_t *P = ring + (q % kEnergyBuf) * L2;
+            if (q == t0) v = *reinterpret_cast<const ulonglong2 *>(P + xy);
+            uint64_t a[6], b[6], eA1, eB1;
+            bonds(P, ring + ((q + 1) % kEnergyBuf) * L2, 0ull, a);
+            bonds(ring + ((q + 1) % kEnergyBuf) * L2, ring + ((q + 2) % kEnergyBuf) * L2, q + 2 == Lt ? apbc : 0ull, b);
+            tree12(a, b, eA1, eB1);
+            uint64_t s16a;
+            csa(s16a, eights, eights, eA1, eB1);
+            const uint64_t carry = sixteens & s16a;
+            sixteens ^= s16a;
+            ripple(carry);
+        }
+    }
+    // the thread's count: ones .. sixteens, then the 32s
+    uint64_t c[kPlanes];
+    c[0] = ones;
+    c[1] = twos;
+    c[2] = fours;
+    c[3] = eights;
+    c[4] = sixteens;
+#pragma unroll
+    for (int p = 5; p < kPlanes; ++p) c[p] = p - 5 < kThirty ? c32[p - 5 < kThirty ? p - 5 : 0] : 0ull;
+    // warp sum of the bitsliced counters; after the round with offset o a
+    // lane's count is below 6 RUN (32 / o), so fewer planes need adding
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int o = 16 >> r;
+        constexpr int base = 5 + kThirty;  // planes of one thread's count
+        uint64_t carry = 0;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            if (p < base + r + 1) {
+                const uint64_t other = __shfl_down_sync(0xffffffffu, c[p], o);
+                const uint64_t sum = c[p] ^ other ^ carry;
+                carry = (c[p] & other) | (carry & (c[p] ^ other));
+                c[p] = sum;
+            }
+        }
+    }
+    {
+        const int lane = tid & 31;
+        int v0 = 0, v1 = 0;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) {
+            const uint64_t cp = __shfl_sync(0xffffffffu, c[p], 0);
+            v0 |= (int)((cp >> lane) & 1ull) << p;
+            v1 |= (int)((cp >> (lane + 32)) & 1ull) << p;
+        }
+        if (v0) atomicAdd(&cnt[lane], v0);
+        if (v1) atomicAdd(&cnt[lane + 32], v1);
+    }
+    __syncthreads();
+    for (int b = tid; b < 64; b += kT)
+        if (cnt[b]) atomicAdd(&g.U[(size_t)s * 64 + b], cnt[b]);
+}
+
+template <int L, int RUN>
+static cudaError_t launch_energy_l(const Group &g, cudaStream_t st) {
+    constexpr size_t sm = (size_t)kEnergyBuf * L * L * sizeof(uint64_t);
+    if (sm > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_energy_l<L, RUN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(g.nslots, (g.Ltau + RUN - 1) / RUN);
+    count_launches(1);
+    k_energy_l<L, RUN><<<grid, energy_threads<L>(), sm, st>>>(g);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_energy_generic(const Group &g, cudaStream_t st) {
     // one thread per two site words; a ring of kEnergyBuf planes in shared memory
     const int L2 = g.L * g.L;
     const int threads = (L2 / 2 + 31) / 32 * 32;
     const size_t sm = (size_t)kEnergyBuf * L2 * sizeof(uint64_t);
     if (sm > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const cudaError_t e = cudaFuncSetAttribute(k_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
     }
     dim3 grid(g.nslots, (g.Ltau + kEnergyRun - 1) / kEnergyRun);
     count_launches(1);
     k_energy<<<grid, threads, sm, st>>>(g);
     return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const Group &g, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(g.U, 0, sizeof(int32_t) * (size_t)g.nslots * 64, st);
+    if (e != cudaSuccess) return e;
+    // runs of 256 planes halve the final warp sums per word where L_tau
+    // leaves enough blocks (4.5 waves of 456 resident blocks at the 256-slot
+    // L = 24, L_tau = 2048 state: 0.55 -> 0.52 ms)
+    const bool long_runs = g.Ltau >= 1024;
+    switch (g.L) {
+        case 8: return long_runs ? launch_energy_l<8, 256>(g, st) : launch_energy_l<8, 128>(g, st);
+        case 12: return long_runs ? launch_energy_l<12, 256>(g, st) : launch_energy_l<12, 128>(g, st);
+        case 16: return long_runs ? launch_energy_l<16, 256>(g, st) : launch_energy_l<16, 128>(g, st);
+        case 20: return long_runs ? launch_energy_l<20, 256>(g, st) : launch_energy_l<20, 128>(g, st);
+        case 24: return long_runs ? launch_energy_l<24, 256>(g, st) : launch_energy_l<24, 128>(g, st);
+        default: return launch_energy_generic(g, st);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -243,68 +468,107 @@ __global__ void __launch_bounds__(64) k_pt_decide(Group g, uint32_t m, uint32_t 
     for (int j = 0; j < K; ++j) g.U[((size_t)wr * K + j) * 64 + b] = (int32_t)((E[j] + three_n) / 2);
 }
 
-// Apply the swaps of one tempering step to the spin words: for every site of
-// every (w, r), walk the ladder and exchange the masked bits of positions i
-// and i+1 in the same order as the decisions.
-__global__ void k_pt_apply(Group g) {
-    constexpr int B = 8;  // slots loaded together (independent loads in flight)
-    const int K = g.K;
-    const size_t total = (size_t)g.W * g.R * g.N;
-    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const size_t wr = idx / g.N, n = idx % g.N;
-        const uint32_t *M = g.swapmask + wr * (K - 1) * 2;
-        uint64_t *base = g.S + wr * K * (size_t)g.N + n;
-        // cur: slot i0 after the swaps of pairs < i0 (cur0: as loaded)
-        uint64_t cur = base[0], cur0 = cur;
-        for (int i0 = 0; i0 + 1 < K; i0 += B) {
-            const int nb = min(B, K - 1 - i0);  // pairs i0 .. i0 + nb - 1, slots i0 + 1 .. i0 + nb
-            uint64_t msk[B];
-            uint64_t any = 0;
-#pragma unroll
-            for (int k = 0; k < B; ++k) {
-                msk[k] = k < nb ? ((uint64_t)__ldg(&M[2 * (i0 + k)]) | ((uint64_t)__ldg(&M[2 * (i0 + k) + 1]) << 32)) : 0ull;
-                any |= msk[k];
-            }
-            if (!any) {
-                // no swap among these pairs: slots i0 + 1 .. i0 + nb keep their bits
-                if (cur != cur0) base[(size_t)i0 * g.N] = cur;
-                cur = cur0 = base[(size_t)(i0 + nb) * g.N];
-                continue;
-            }
-            uint64_t v[B];
-#pragma unroll
-            for (int k = 0; k < B; ++k)
-                if (k < nb) v[k] = base[(size_t)(i0 + 1 + k) * g.N];
-#pragma unroll
-            for (int k = 0; k < B; ++k) {
-                if (k < nb) {
-                    uint64_t nxt = v[k];
-                    const uint64_t nxt0 = nxt;
-                    const uint64_t d = (cur ^ nxt) & msk[k];
-                    cur ^= d;
-                    nxt ^= d;
-                    if (cur != cur0) base[(size_t)(i0 + k) * g.N] = cur;
-                    cur = nxt;
-                    cur0 = nxt0;
+// Apply the swaps of one tempering step to the spin words.  A block serves
+// one (w, r) and a range of sites; it first lists the ladder pairs whose swap
+// mask is not zero (the same for all its sites), and every thread then walks
+// only those pairs in increasing order, exchanging the masked bits of
+// positions i and i + 1 as the decisions did.  Consecutive listed pairs form
+// a chain (a configuration can move several positions in one step); a slot is
+// read only when a listed pair touches it and written only when its bits
+// changed.  Slots are loaded for eight listed pairs at a time (independent
+// loads in flight).
+constexpr int kApplyThreads = 256;
+
+__global__ void __launch_bounds__(kApplyThreads) k_pt_apply(Group g) {
+    constexpr int B = 8;
+    __shared__ uint64_t msk[kMaxK];
+    __shared__ int act[kMaxK];
+    __shared__ int nact;
+    const int K = g.K, N = g.N;
+    for (int wr = blockIdx.y; wr < g.W * g.R; wr += gridDim.y) {
+        const uint32_t *M = g.swapmask + (size_t)wr * (K - 1) * 2;
+        if (threadIdx.x < 32) {
+            // warp 0 lists the pairs with a swap, in increasing order
+            int n0 = 0;
+            for (int i0 = 0; i0 + 1 < K; i0 += 32) {
+                const int i = i0 + (int)threadIdx.x;
+                uint64_t m = 0;
+                if (i + 1 < K) m = (uint64_t)M[2 * i] | ((uint64_t)M[2 * i + 1] << 32);
+                const unsigned ball = __ballot_sync(0xffffffffu, m != 0);
+                if (m) {
+                    const int at = n0 + __popc(ball & ((1u << threadIdx.x) - 1u));
+                    act[at] = i;
+                    msk[at] = m;
                 }
+                n0 += __popc(ball);
             }
+            if (threadIdx.x == 0) nact = n0;
         }
-        if (cur != cur0) base[(size_t)(K - 1) * g.N] = cur;
+        __syncthreads();
+        const int na = nact;
+        uint64_t *const slot0 = g.S + (size_t)wr * K * N;
+        for (int n = blockIdx.x * kApplyThreads + threadIdx.x; na > 0 && n < N; n += gridDim.x * kApplyThreads) {
+            uint64_t *base = slot0 + n;
+            uint64_t cur = 0, cur0 = 0;  // slot prev + 1 after the swaps so far, and as loaded
+            int prev = -2;               // the last pair walked
+            for (int a0 = 0; a0 < na; a0 += B) {
+                const int nb = min(B, na - a0);
+                uint64_t vn[B], vs[B];
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    if (k < nb) {
+                        const int p = act[a0 + k], pp = k == 0 ? prev : act[a0 + k - 1];
+                        vn[k] = base[(size_t)(p + 1) * N];
+                        vs[k] = p != pp + 1 ? base[(size_t)p * N] : 0ull;  // a chain starts at p
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < B; ++k) {
+                    if (k < nb) {
+                        const int p = act[a0 + k], pp = k == 0 ? prev : act[a0 + k - 1];
+                        if (p != pp + 1) {
+                            if (pp >= 0 && cur != cur0) base[(size_t)(pp + 1) * N] = cur;
+                            cur = cur0 = vs[k];
+                        }
+                        uint64_t nxt = vn[k];
+                        const uint64_t nxt0 = nxt;
+                        const uint64_t d = (cur ^ nxt) & msk[a0 + k];
+                        cur ^= d;
+                        nxt ^= d;
+                        if (cur != cur0) base[(size_t)p * N] = cur;
+                        cur = nxt;
+                        cur0 = nxt0;
+                    }
+                }
+                prev = act[a0 + nb - 1];
+            }
+            if (na > 0 && cur != cur0) base[(size_t)(prev + 1) * N] = cur;
+        }
+        __syncthreads();  // the list is rebuilt for the next (w, r)
     }
 }
+
+static cudaError_t launch_apply(const Group &g, cudaStream_t st);
 
 cudaError_t launch_tempering(const Group &g, uint32_t m, uint64_t seed, cudaStream_t st) {
     if (g.K < 2) return cudaSuccess;
     count_launches(1);
     k_pt_decide<<<g.W * g.R, 64, 0, st>>>(g, m, (uint32_t)seed, (uint32_t)(seed >> 32));
-    cudaError_t e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const size_t total = (size_t)g.W * g.R * g.N;
-    long long blocks = (long long)((total + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    return launch_apply(g, st);
+}
+
+static cudaError_t launch_apply(const Group &g, cudaStream_t st) {
+    // one resident wave of blocks (2048 threads per SM) shared out over the
+    // (w, r) rows; a block strides over its row's sites
+    const int wr = g.W * g.R;
+    long long bx = (152LL * 2048 / kApplyThreads + wr - 1) / wr;
+    const long long need = (g.N + kApplyThreads - 1) / kApplyThreads;
+    if (bx > need) bx = need;
+    if (bx < 1) bx = 1;
     count_launches(1);
-    k_pt_apply<<<(int)blocks, 256, 0, st>>>(g);
+    k_pt_apply<<<dim3((unsigned)bx, (unsigned)(wr < 65535 ? wr : 65535)), kApplyThreads, 0, st>>>(g);
     return cudaGetLastError();
 }
 

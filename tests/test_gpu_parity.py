@@ -95,6 +95,44 @@ def test_tempering_matches_oracle(algo):
     assert ctx.qsg_read_accepts().sum() > 0
 
 
+def test_tempering_chains_over_a_long_ladder_match_oracle():
+    """A dense ladder accepts most swaps, so a configuration often moves
+    several positions in one tempering step: the moves walk runs of
+    consecutive swapped pairs, and pairs without a swap are skipped."""
+    shape = Q.Shape(4, 8, 70, 2, 24, Q.HEATBATH, Q.APBC)
+    lad = workloads.uniform_ladder(0.30, 0.33, 24)
+    ctx, orc = _pair(shape, lad, seed=5)
+    for _ in range(6):
+        ctx.qsg_sweep(1)
+        orc.sweep(1)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    assert np.array_equal(ctx.qsg_read_accepts(), orc.accepts())
+    acc = ctx.qsg_read_accepts()
+    assert acc.sum() > 6 * 23 * 70 * 2 // 4  # most pairs swap
+
+
+@pytest.mark.parametrize("L,Ltau,boundary", [(8, 1026, Q.APBC), (12, 126, Q.PBC), (16, 1024, Q.APBC),
+                                             (20, 126, Q.APBC), (24, 1026, Q.PBC), (24, 130, Q.APBC),
+                                             (10, 70, Q.PBC)])
+def test_energies_of_every_compiled_lattice_size_match_oracle(L, Ltau, boundary):
+    # the energy pass has a kernel with L compiled in for L = 8, 12, 16, 20,
+    # 24 (runs of 256 planes from L_tau = 1024, else 128; L_tau = 2 mod 4
+    # leaves a two-plane step) and a generic one for the other sizes
+    shape = Q.Shape(L, Ltau, 1, 2, 3, Q.METROPOLIS, boundary)
+    lad = workloads.uniform_ladder(0.25, 0.35, 3)
+    ctx, orc = _pair(shape, lad, seed=L + Ltau)
+    for _ in range(3):
+        ctx.qsg_sweep(1)
+        orc.sweep(1)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+
+
 @pytest.mark.parametrize("Ltau,boundary", [(70, Q.APBC), (130, Q.PBC), (130, Q.APBC)])
 def test_energies_with_ragged_plane_runs_match_oracle(Ltau, boundary):
     # the energy pass takes 128-plane runs, four planes per step: L_tau = 70
