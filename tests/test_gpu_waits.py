@@ -63,3 +63,24 @@ def test_wait_limit_is_validated():
         with pytest.raises(Q.QSGError):
             ctx.qsg_set_option(Q.OPT_WAIT_LIMIT, bad)
     ctx.qsg_set_option(Q.OPT_WAIT_LIMIT, 1 << 22)
+
+
+def test_asynchronous_read_reports_the_flag_when_waited_for():
+    """qsg_read_correlators_async queues its copies without checking the
+    device flag; qsg_wait_correlators reports it once the copies are done,
+    and a context whose waits never gave up reports nothing."""
+    shape = Q.Shape(8, 256, 64, 2, 1, Q.HEATBATH, Q.PBC)
+    lad = np.array([0.3])
+    copy_stream = torch.cuda.Stream()
+    bad = _run(shape, lad, 7, wait_limit=0)
+    bad.qsg_read_correlators_async(bad.correlator_buffers(pinned=True), copy_stream)
+    with pytest.raises(Q.QSGError) as e:
+        bad.qsg_wait_correlators()
+    assert e.value.status == -4
+    good = _run(shape, lad, 7)
+    out = good.correlator_buffers(pinned=True)
+    good.qsg_read_correlators_async(out, copy_stream)
+    good.qsg_wait_correlators()
+    ref = good.qsg_read_correlators()
+    for key in ("C", "Q2", "q2"):
+        assert np.array_equal(out[key], ref[key]), key
