@@ -30,6 +30,9 @@
 namespace qsg {
 
 constexpr int kMaxTripleR = 8;  // three-replica terms for 3 <= R <= 8
+// Replica pairs whose Q^2 sums a block keeps in shared memory; with more
+// (R > 128) every slice adds its pair sums straight to the global ones.
+constexpr int kMaxSharedPairs = 8192;
 
 __host__ __device__ constexpr int bit_length(int n) { return n == 0 ? 0 : 1 + bit_length(n >> 1); }
 
@@ -151,16 +154,18 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
     const int R = g.R, Lt = g.Ltau, bd = blockDim.x, tid = threadIdx.x;
     const int npair = R * (R - 1) / 2;
     const bool do3 = triples && R >= 3 && R <= kMaxTripleR;
-    // [pair] per-pair sums of Q^2; [2][L/2+1][thread] the thread's G and F3 sums
-    // (kept in shared memory to spare registers); then (triples only)
-    // [pair][dir][word][thread] packed column/row difference counts and
-    // [pair][thread] overlaps
+    const bool pp_shared = npair <= kMaxSharedPairs;
+    const int npsh = pp_shared ? npair : 0;
+    // [pair] per-pair sums of Q^2 (up to kMaxSharedPairs pairs); [2][L/2+1]
+    // [thread] the thread's G and F3 sums (kept in shared memory to spare
+    // registers); then (triples only) [pair][dir][word][thread] packed
+    // column/row difference counts and [pair][thread] overlaps
     unsigned long long *ppsh = reinterpret_cast<unsigned long long *>(ot_smem);
-    long long *accsh = reinterpret_cast<long long *>(ot_smem + (size_t)npair * 8);
-    const size_t o_n = (size_t)npair * 8 + (size_t)2 * (H + 1) * bd * 8;
+    long long *accsh = reinterpret_cast<long long *>(ot_smem + (size_t)npsh * 8);
+    const size_t o_n = (size_t)npsh * 8 + (size_t)2 * (H + 1) * bd * 8;
     uint32_t *nsh = reinterpret_cast<uint32_t *>(ot_smem + o_n);
     int16_t *qsh = reinterpret_cast<int16_t *>(ot_smem + o_n + (size_t)npair * 2 * NP * 4 * bd);
-    for (int i = tid; i < npair; i += bd) ppsh[i] = 0ull;
+    for (int i = tid; i < npsh; i += bd) ppsh[i] = 0ull;
 #pragma unroll
     for (int d = 0; d <= H; ++d) {
         accsh[(size_t)d * bd + tid] = 0;
@@ -169,6 +174,8 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
     __syncthreads();
     const int pb = blockIdx.x / 64, b = blockIdx.x % 64;
     const int p = p0 + pb, w = p / g.K, j = p % g.K;
+    unsigned long long *ppg =
+        reinterpret_cast<unsigned long long *>(g.PPacc) + ((size_t)(w * 64 + b) * g.K + j) * npair;
     const size_t plane = (size_t)Lt * NW;
     const uint64_t *base = P + (size_t)pb * R * 64 * plane + (size_t)b * plane;
 
@@ -185,7 +192,7 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
                 const int q0 = L * L - 2 * A;
                 const unsigned long long q2 = (unsigned long long)(q0 * q0);
                 p2 += (long long)q2;
-                atomicAdd(&ppsh[pi], q2);
+                atomicAdd(pp_shared ? &ppsh[pi] : &ppg[pi], q2);
                 const unsigned long long q4 = q2 * q2;
                 p4lo += q4 & 0xFFFFFFFFull;
                 p4hi += q4 >> 32;
@@ -260,9 +267,7 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
     }
 
     __syncthreads();
-    for (int i = tid; i < npair; i += bd)
-        atomicAdd(reinterpret_cast<unsigned long long *>(&g.PPacc[((size_t)(w * 64 + b) * g.K + j) * npair + i]),
-                  ppsh[i]);
+    for (int i = tid; i < npsh; i += bd) atomicAdd(&ppg[i], ppsh[i]);
     // block reduction: warp shuffles, one atomic per warp and quantity
     auto wsum = [](long long v) {
 #pragma unroll
@@ -296,7 +301,7 @@ __global__ void __launch_bounds__(128, 3) k_onetime(Group g, int p0, const uint6
 
 size_t onetime_smem_bytes(const Group &g, int triples, int threads) {
     const int npair = g.R * (g.R - 1) / 2;
-    const size_t pp = (size_t)npair * 8 + (size_t)2 * (g.L / 2 + 1) * threads * 8;
+    const size_t pp = (size_t)(npair <= kMaxSharedPairs ? npair : 0) * 8 + (size_t)2 * (g.L / 2 + 1) * threads * 8;
     if (!triples || g.R < 3 || g.R > kMaxTripleR) return pp;
     const int np4 = 4 * ((g.L + 3) / 4);  // packed count bytes per vector
     return pp + (size_t)npair * (2 * np4 + 2) * threads;

@@ -565,6 +565,58 @@ def test_many_ladder_pairs_in_one_measurement_batch():
         assert np.array_equal(got["q2_raw"][b], ref["q2_raw"][0])
 
 
+@pytest.mark.parametrize("R", [128, 129, 1023])
+def test_replica_counts_up_to_the_largest_match_oracle(R):
+    """Up to 128 replicas (8,128 pairs) a block of the one-time pass keeps the
+    per-pair Q^2 sums in shared memory; from 129 (8,256 pairs) up to the
+    largest count a shape may have, 1023 (522,753 pairs), every slice adds
+    them straight to the global sums.  Correlator and pair sums match the
+    oracle bit for bit."""
+    shape = Q.Shape(2, 4, 1, R, 1, Q.HEATBATH, Q.PBC)
+    lad = np.array([0.3])
+    ctx, orc = _pair(shape, lad, seed=R)
+    ctx.qsg_sweep(2)
+    orc.sweep(2)
+    ctx.qsg_measure_correlators()
+    orc.measure()
+    _check_corr(ctx.qsg_read_correlators(raw=True), orc.read())
+    assert np.array_equal(ctx.qsg_read_pair_overlaps(), orc.read_pair_overlaps())
+
+
+def test_largest_ladder_matches_oracle():
+    """128 k values (the largest ladder): 127 pairs per tempering step, the
+    moves list up to 127 swapped pairs in batches of eight."""
+    shape = Q.Shape(4, 8, 70, 2, 128, Q.METROPOLIS, Q.APBC)
+    lad = workloads.uniform_ladder(0.2, 0.5, 128)
+    ctx, orc = _pair(shape, lad, seed=17)
+    for _ in range(4):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+    assert np.array_equal(ctx.qsg_read_accepts(), orc.accepts())
+    ctx.qsg_measure_correlators()
+    orc.measure()
+    _check_corr(ctx.qsg_read_correlators(raw=True), orc.read())
+
+
+def test_longest_ltau_matches_oracle():
+    """L_tau = 65,536 (the longest a shape may have): wavefront sweeps over
+    1,024 chunks per slot, energies in 512 runs per slot, tempering steps."""
+    shape = Q.Shape(4, 65536, 1, 2, 2, Q.HEATBATH, Q.APBC)
+    lad = np.array([0.2998, 0.3])
+    ctx, orc = _pair(shape, lad, seed=65)
+    for _ in range(2):
+        ctx.qsg_sweep(2)
+        orc.sweep(2)
+        ctx.qsg_tempering_swap()
+        orc.swap()
+        assert np.array_equal(ctx.qsg_read_energies(), orc.energies())
+    assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
+
+
 @pytest.mark.parametrize("pinned", [False, True])
 def test_correlator_readback_into_caller_buffers(pinned):
     """Reading into caller-owned (page-locked or pageable) buffers gives the
