@@ -26,41 +26,58 @@ __device__ __forceinline__ uint64_t transpose_step(uint64_t w, bool upper, uint6
 }
 
 // scratch layout for a batch of (w, j) pairs: [pair][r][b][tau][nwx].
-// One warp per (slot, tau, 64-site group): lane l loads the multispin words of
-// sites l and l + 32 (bit b = sample b), transposes the 64 x 64 bit block in
-// registers and ends up holding the x-packed words of samples l and l + 32.
-__global__ void k_transpose(Group g, int p0, int npairs, uint64_t *P) {
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long total = (long long)npairs * g.R * g.Ltau * g.nwx;
-    if (warp >= total) return;
-    const int L2 = g.L * g.L;
-    const int gx = (int)(warp % g.nwx);
-    const int t = (int)((warp / g.nwx) % g.Ltau);
-    const int sb = (int)(warp / ((long long)g.nwx * g.Ltau));
+// One block per (slot of the batch, run of kTrRun tau planes), one warp per
+// plane: for every 64-site group the warp's lane l loads the multispin words
+// of sites l and l + 32 (bit b = sample b, one coalesced 512-byte read),
+// transposes the 64 x 64 bit block in registers and holds the x-packed words
+// of samples l and l + 32, which it puts in shared memory.  The block then
+// writes each sample's kTrRun x nwx words, contiguous in the scratch, as one
+// coalesced run (a sample's words of one plane are nwx words long and the
+// next sample's begin L_tau nwx words later, so a warp storing its two words
+// straight would write 64 separate 8-byte pieces).
+constexpr int kTrRun = 8;  // tau planes per block (warps of 32 threads)
+
+__global__ void __launch_bounds__(32 * kTrRun) k_transpose(Group g, int p0, int npairs, uint64_t *P) {
+    extern __shared__ uint64_t trs[];  // [64 samples][kTrRun * nwx + 1 (padding)]
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int nwx = g.nwx, Lt = g.Ltau, L2 = g.L * g.L;
+    const int pitch = kTrRun * nwx + 1;
+    const int sb = blockIdx.x;  // slot of the batch: (pair, replica)
+    const int t0 = blockIdx.y * kTrRun, nt = min(kTrRun, Lt - t0);
     const int pb = sb / g.R, r = sb % g.R;
     const int p = p0 + pb, w = p / g.K, j = p % g.K;
     const size_t s = ((size_t)w * g.R + r) * g.K + j;
-    const uint64_t *src = g.S + s * g.N + (size_t)t * L2;
-    const int s0 = gx * 64 + lane, s1 = s0 + 32;
-    const uint64_t w0 = s0 < L2 ? src[s0] : 0ull;
-    const uint64_t w1 = s1 < L2 ? src[s1] : 0ull;
-    // j = 32: rows l and l + 32 are both in this lane
-    uint64_t a0 = (w0 & 0xFFFFFFFFull) | (w1 << 32);
-    uint64_t a1 = (w0 >> 32) | (w1 & 0xFFFFFFFF00000000ull);
-    a0 = transpose_step<16>(a0, lane & 16, 0x0000FFFF0000FFFFull);
-    a1 = transpose_step<16>(a1, lane & 16, 0x0000FFFF0000FFFFull);
-    a0 = transpose_step<8>(a0, lane & 8, 0x00FF00FF00FF00FFull);
-    a1 = transpose_step<8>(a1, lane & 8, 0x00FF00FF00FF00FFull);
-    a0 = transpose_step<4>(a0, lane & 4, 0x0F0F0F0F0F0F0F0Full);
-    a1 = transpose_step<4>(a1, lane & 4, 0x0F0F0F0F0F0F0F0Full);
-    a0 = transpose_step<2>(a0, lane & 2, 0x3333333333333333ull);
-    a1 = transpose_step<2>(a1, lane & 2, 0x3333333333333333ull);
-    a0 = transpose_step<1>(a0, lane & 1, 0x5555555555555555ull);
-    a1 = transpose_step<1>(a1, lane & 1, 0x5555555555555555ull);
-    const size_t row0 = ((size_t)sb * 64 + lane) * g.Ltau + t, row1 = row0 + (size_t)32 * g.Ltau;
-    P[row0 * g.nwx + gx] = a0;
-    P[row1 * g.nwx + gx] = a1;
+    if (sb >= npairs * g.R) return;  // the grid is exact: never taken
+    if (wp < nt) {
+        const int t = t0 + wp;
+        const uint64_t *src = g.S + s * g.N + (size_t)t * L2;
+        for (int gx = 0; gx < nwx; ++gx) {
+            const int s0 = gx * 64 + lane, s1 = s0 + 32;
+            const uint64_t w0 = s0 < L2 ? src[s0] : 0ull;
+            const uint64_t w1 = s1 < L2 ? src[s1] : 0ull;
+            // j = 32: rows l and l + 32 are both in this lane
+            uint64_t a0 = (w0 & 0xFFFFFFFFull) | (w1 << 32);
+            uint64_t a1 = (w0 >> 32) | (w1 & 0xFFFFFFFF00000000ull);
+            a0 = transpose_step<16>(a0, lane & 16, 0x0000FFFF0000FFFFull);
+            a1 = transpose_step<16>(a1, lane & 16, 0x0000FFFF0000FFFFull);
+            a0 = transpose_step<8>(a0, lane & 8, 0x00FF00FF00FF00FFull);
+            a1 = transpose_step<8>(a1, lane & 8, 0x00FF00FF00FF00FFull);
+            a0 = transpose_step<4>(a0, lane & 4, 0x0F0F0F0F0F0F0F0Full);
+            a1 = transpose_step<4>(a1, lane & 4, 0x0F0F0F0F0F0F0F0Full);
+            a0 = transpose_step<2>(a0, lane & 2, 0x3333333333333333ull);
+            a1 = transpose_step<2>(a1, lane & 2, 0x3333333333333333ull);
+            a0 = transpose_step<1>(a0, lane & 1, 0x5555555555555555ull);
+            a1 = transpose_step<1>(a1, lane & 1, 0x5555555555555555ull);
+            trs[(size_t)lane * pitch + wp * nwx + gx] = a0;
+            trs[(size_t)(lane + 32) * pitch + wp * nwx + gx] = a1;
+        }
+    }
+    __syncthreads();
+    // sample b's words of planes t0 .. t0 + nt - 1 are contiguous in the scratch
+    const int n = nt * nwx;
+    uint64_t *dst = P + ((size_t)sb * 64 * Lt + t0) * nwx;
+    for (int b = wp; b < 64; b += kTrRun)
+        for (int o = lane; o < n; o += 32) dst[(size_t)b * Lt * nwx + o] = trs[(size_t)b * pitch + o];
 }
 
 // One block per (slot of the batch, sample bit): all lags of one sample.
@@ -121,9 +138,16 @@ cudaError_t launch_measure(const Group &g, uint64_t *scratch, size_t scratch_wor
     }
     for (int p0 = 0; p0 < npairs_total; p0 += batch) {
         const int np = min(batch, npairs_total - p0);
-        const long long warps = (long long)np * g.R * g.Ltau * g.nwx;
+        const size_t tr_smem = (size_t)64 * (kTrRun * g.nwx + 1) * sizeof(uint64_t);
+        if (tr_smem > 48 * 1024) {
+            const cudaError_t ea = cudaFuncSetAttribute(k_transpose, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                        (int)tr_smem);
+            if (ea != cudaSuccess) return ea;
+        }
         count_launches(1);
-        k_transpose<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(g, p0, np, scratch);
+        // slots along x (up to 2^31 - 1), runs of planes along y (L_tau / 8 <= 8192)
+        k_transpose<<<dim3((unsigned)(np * g.R), (unsigned)((g.Ltau + kTrRun - 1) / kTrRun)), 32 * kTrRun, tr_smem,
+                      st>>>(g, p0, np, scratch);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (tensor) {
