@@ -412,7 +412,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
                     for (int k = 0; k < nw; ++k) {
                         const int hh = hh0 + k;
-                        expand_word(rowp, k ? w1 : w0, t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
+                        // a word past the lattice's last site is never read (the
+                        // MMAs of the last chunk stop at its last word with a site)
+                        if (L2 - kc * kChunk - 64 * hh > 0)
+                            expand_word(rowp, k ? w1 : w0, t < Lt ? L2 - kc * kChunk - 64 * hh : 0, hh, row);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -500,6 +503,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         // A chunk, a commit frees that chunk for the next item's A block
         if (lane == 0) {
             const uint32_t id128 = idesc_e4m3(128), id256 = idesc_e4m3(256);
+            // 32-site steps of the last chunk: those of its 64-site words that
+            // hold a lattice site (the bit-interleaved order spreads a word's
+            // sites over its whole 64-byte span)
+            const int nk_last = min(kChunk / 32, 2 * ((L2 - (NC - 1) * kChunk + 63) / 64));
             const uint32_t sA0 = smem_u32(sA), sB0 = smem_u32(sB);
             uint32_t a_par = 0u, b_par = 0u, n_t = 0;
             int bs = 0;
@@ -520,10 +527,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
                             if (ok) {
                                 const uint32_t ab = sA0 + kc * kChunkBytes;
+                                const int nk = kc == NC - 1 ? nk_last : kChunk / 32;
 #pragma unroll
                                 for (int kk = 0; kk < kChunk / 32; ++kk)
-                                    mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(ab + kk * 32), id128,
-                                           (kc > 0 || kk > 0) ? 1u : 0u);
+                                    if (kk < nk)
+                                        mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(ab + kk * 32), id128,
+                                               (kc > 0 || kk > 0) ? 1u : 0u);
                                 issued = true;
                             }
                             if (last) mma_commit(&ctl.aempty[kc]);
@@ -544,10 +553,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             asm volatile("tcgen05.fence::after_thread_sync;\n");
                             if (ok) {
                                 const uint32_t ab = sA0 + kc * kChunkBytes, bb = sB0 + bs * kStageBytes;
+                                const int nk = kc == NC - 1 ? nk_last : kChunk / 32;
 #pragma unroll
                                 for (int kk = 0; kk < kChunk / 32; ++kk)
-                                    mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(bb + kk * 32), idesc,
-                                           (kc > 0 || kk > 0) ? 1u : 0u);
+                                    if (kk < nk)
+                                        mma_f8(d, sdesc_sw128(ab + kk * 32), sdesc_sw128(bb + kk * 32), idesc,
+                                               (kc > 0 || kk > 0) ? 1u : 0u);
                                 issued = true;
                             }
                             mma_commit(&ctl.bempty[bs]);
