@@ -45,7 +45,9 @@
  *
  * Conventions: every call returns a qsg_status and nothing is thrown across
  * the ABI.  Device work is enqueued on the caller's CUDA stream; calls named
- * read_* / get_* / set_* synchronise that stream, no other call does.  The
+ * read_* / get_* / set_* synchronise that stream (except
+ * qsg_read_correlators_async and the *_device calls), no other call does
+ * (qsg_wait_correlators waits for the asynchronous copies only).  The
  * library allocates no device memory: the caller passes one device workspace
  * of qsg_workspace_bytes() bytes, owned by the caller and used by the library
  * until qsg_destroy().  Host pointers passed to a call are read or written
@@ -148,9 +150,10 @@ qsg_status qsg_measure_correlators(qsg_ctx *ctx);
  * C_acc then Q_acc then P_acc in the same layouts.  Synchronises the stream. */
 qsg_status qsg_read_correlators(qsg_ctx *ctx, int32_t group, double *C, double *Q2, double *q2, int64_t *raw);
 
-/* qsg_read_correlators without the host wait: the finish runs on the
- * context's stream and the copies (same outputs and layouts) on copy_stream
- * (a cudaStream_t other than the context's), which waits for the finish.  The
+/* qsg_read_correlators without the host wait: the finish and the copies
+ * (same outputs and layouts) run on copy_stream (a cudaStream_t other than
+ * the context's) once the work queued so far on the context's stream is done,
+ * so the context's stream goes on without them.  The
  * call returns once the work is queued; the host buffers (page-locked for the
  * copies to overlap compute) hold the results once qsg_wait_correlators
  * returns or copy_stream has been synchronised, and must stay allocated until

@@ -228,8 +228,8 @@ struct qsg_ctx {
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> joins;
     cudaEvent_t fork = nullptr;
-    // qsg_read_correlators_async: the finish's completion on `stream` and the
-    // completion of the copies on the caller's stream, which every later
+    // qsg_read_correlators_async: the point on `stream` the finish and copies
+    // on the caller's stream wait for, and their completion, which every later
     // writer of the correlator buffers waits for
     cudaEvent_t fin_ev = nullptr, copy_ev = nullptr;
     bool copy_pending = false;
@@ -672,9 +672,12 @@ qsg_status qsg_read_correlators_async(qsg_ctx *ctx, int32_t group, double *C, do
     if (!ctx->copy_ev) QSG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->copy_ev, cudaEventDisableTiming));
     if (!ctx->h_flag) QSG_CUDA(ctx, cudaHostAlloc((void **)&ctx->h_flag, sizeof(int), cudaHostAllocDefault));
     const Group &g = ctx->groups[group];
-    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, ctx->stream));
+    // the finish runs on the copy stream too, once the context's stream has
+    // done the measurements: it writes only what the copies read, and the
+    // next writer of the sums waits for the copies
     QSG_CUDA(ctx, cudaEventRecord(ctx->fin_ev, ctx->stream));
     QSG_CUDA(ctx, cudaStreamWaitEvent(cs, ctx->fin_ev, 0));
+    QSG_CUDA(ctx, launch_finish(g, ctx->n_meas, cs));
     if (qsg_status o = copy_correlators(ctx, g, C, Q2, q2, raw, cs)) return o;
     QSG_CUDA(ctx, cudaMemcpyAsync(ctx->h_flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, cs));
     QSG_CUDA(ctx, cudaEventRecord(ctx->copy_ev, cs));
