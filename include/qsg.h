@@ -334,7 +334,7 @@ qsg_status qsg_set_counters(qsg_ctx *ctx, uint32_t sweeps, uint32_t swaps, int64
  *                         otherwise a multiple of 16 that divides every L_tau)
  *   QSG_OPT_WAVEFRONT_VARIANT  form of the wavefront kernel, process-wide:
  *                         0 = one work unit per block with L compiled in
- *                         (L = 20, 24; 72 registers, three blocks of 288
+ *                         (L = 8, 12, 16, 20, 24; 72 registers, three blocks of 288
  *                         threads per SM at L = 24), four tau planes per
  *                         block barrier; other L use the
  *                         generic kernel;

@@ -19,7 +19,7 @@
 //    the whole unit (they are read from global memory once, and no shared
 //    copy is kept), so a block needs 16 planes of shared memory only;
 //  * 72 registers per thread: three blocks of 288 threads per SM at L = 24
-//    (four of 200 at L = 20) instead of two;
+//    (four of 200 at L = 20, seven of 128 at L = 16) instead of two;
 //  * PB = 4 planes per block barrier (PB = 2 as a variant).  With four
 //    planes per step the ring allows a prefetch distance of 10 planes: the
 //    planes of step q + 4 are issued after the barrier of step q - 4 and all
@@ -82,6 +82,7 @@ __device__ __forceinline__ void boundary_sites(const Group &g, int c, uint64_t *
 }
 
 // 72 registers: three blocks of 288 threads per SM at L = 24, four of 200 at L = 20
+// (L = 8, 12, 16 are compiled too: the ragged workloads' smaller lattices)
 constexpr int kUnitRegs = 72;
 
 // One launch per sweep of one group, one unit per block (L^2 / 2 threads).
@@ -358,13 +359,20 @@ cudaError_t launch_unit(const Group &g, int C, int C2, int S1, const uint32_t *s
 template <int ALGO, int PB>
 cudaError_t launch_unit_L(const Group &g, int C, int C2, int S1, const uint32_t *sb, uint32_t sweep, uint64_t seed,
                           unsigned *arrivals, cudaStream_t st) {
-    if (g.L == 24) return launch_unit<ALGO, 24, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
-    return launch_unit<ALGO, 20, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+    switch (g.L) {
+        case 8: return launch_unit<ALGO, 8, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+        case 12: return launch_unit<ALGO, 12, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+        case 16: return launch_unit<ALGO, 16, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+        case 20: return launch_unit<ALGO, 20, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+        default: return launch_unit<ALGO, 24, PB>(g, C, C2, S1, sb, sweep, seed, arrivals, st);
+    }
 }
 
 }  // namespace
 
-bool sweep_unit_supported(const Group &g) { return (g.L == 20 || g.L == 24) && g.Ltau % 16 == 0; }
+bool sweep_unit_supported(const Group &g) {
+    return (g.L == 8 || g.L == 12 || g.L == 16 || g.L == 20 || g.L == 24) && g.Ltau % 16 == 0;
+}
 
 cudaError_t launch_sweep_unit(const Group &g, int planes_per_barrier, int C, int C2, int S1,
                               const uint32_t *sweep_base, uint32_t sweep, uint64_t seed, unsigned *arrivals,

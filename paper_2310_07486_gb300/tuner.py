@@ -32,7 +32,7 @@ _NAMES = {Q.OPT_CHUNK: "chunk", Q.OPT_WAVEFRONT_VARIANT: "variant", Q.OPT_PERSIS
           Q.OPT_GRAPH: "graph", Q.OPT_TAIL: "tail", Q.OPT_UNITS_PER_BLOCK: "upb"}
 DEFAULTS = {"chunk": 0, "variant": 0, "persistent": 0, "graph": 0, "tail": 0, "upb": 0}
 UPB = [1, 2, 4, 8, 16]  # units per block of the generic kernel, tried after the first stage
-COMPILED_L = (20, 24)   # lattice sizes with a compiled one-unit-per-block kernel
+COMPILED_L = (8, 12, 16, 20, 24)  # lattice sizes with a compiled one-unit-per-block kernel
 TAILS = [0, 16, 24, 28, 32, 40, 48, 64]  # slots swept in quarter-length chunks, tried after the rest
 VARIANTS = [0, 1, 2, 3]  # forms of the wavefront kernel (QSG_OPT_WAVEFRONT_VARIANT)
 

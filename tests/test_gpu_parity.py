@@ -692,7 +692,7 @@ def test_wavefront_tail_slots_in_short_chunks_match_oracle(Ltau, chunk, tail):
     assert np.array_equal(_gpu_spins(ctx, shape), orc.spins())
 
 
-@pytest.mark.parametrize("L", [20, 24])
+@pytest.mark.parametrize("L", [8, 12, 16, 20, 24])
 @pytest.mark.parametrize("algo,boundary", [(Q.METROPOLIS, Q.APBC), (Q.HEATBATH, Q.PBC)])
 @pytest.mark.parametrize("Ltau,chunk,tail,variant", [(16, 16, 0, 0), (64, 16, 0, 3), (64, 32, 0, 1),
                                                      (128, 64, 2, 0), (256, 128, 3, 1), (256, 64, 2, 3)])

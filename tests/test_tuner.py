@@ -27,8 +27,10 @@ def test_candidates_cover_persistent_and_graph_only_where_they_apply():
 
 
 def test_units_per_block_stage_only_where_the_generic_kernel_runs():
-    assert not tuner.uses_generic_kernel([Q.Shape(24, 2048, 64, 1, 1), Q.Shape(20, 1024, 64, 1, 1)], variant=0)
-    assert tuner.uses_generic_kernel([Q.Shape(24, 2048, 64, 1, 1), Q.Shape(16, 512, 64, 1, 1)], variant=0)
+    compiled = [Q.Shape(24, 2048, 64, 1, 1), Q.Shape(20, 1024, 64, 1, 1), Q.Shape(16, 512, 64, 1, 1),
+                Q.Shape(12, 256, 64, 1, 1), Q.Shape(8, 128, 64, 1, 1)]
+    assert not tuner.uses_generic_kernel(compiled, variant=0)
+    assert tuner.uses_generic_kernel([Q.Shape(24, 2048, 64, 1, 1), Q.Shape(10, 512, 64, 1, 1)], variant=0)
     assert tuner.uses_generic_kernel([Q.Shape(24, 2048, 64, 1, 1)], variant=2)
     first = list(tuner.candidates([Q.Shape(8, 32, 64, 1, 1)], sweeps_per_call=4))
     assert {c["upb"] for c in first} == {0}  # the first stage keeps the automatic grouping
