@@ -64,6 +64,9 @@ def test_calls_on_null_context_fail_cleanly():
     assert lib.qsg_sweep(None, 1) == -1
     assert lib.qsg_tempering_swap(None) == -1
     assert lib.qsg_measure_correlators(None) == -1
+    assert lib.qsg_read_correlators(None, 0, None, None, None, None) == -1
+    assert lib.qsg_read_correlators_async(None, 0, None, None, None, None, None) == -1
+    assert lib.qsg_wait_correlators(None) == -1
     assert lib.qsg_strerror(-4) == b"bounded device wait gave up"
 
 
