@@ -242,6 +242,7 @@ class Context:
         # torch's caching allocator returns blocks aligned to at least 512 bytes
         self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._pending_out = []  # host buffers of asynchronous reads not yet waited for
         h = ctypes.c_void_p()
         st = self._check(self.lib.qsg_create(ctypes.byref(h), ctypes.cast(self._arr, ctypes.c_void_p), len(self.shapes),
                                              ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
@@ -343,7 +344,7 @@ class Context:
         self._check(self.lib.qsg_read_correlators_async(self.h, group, _ptr(C), _ptr(Q), _ptr(P), None,
                                                         ctypes.c_void_p(int(raw_stream))),
                     "qsg_read_correlators_async")
-        self._pending_out = getattr(self, "_pending_out", []) + [out]
+        self._pending_out.append(out)
 
     def qsg_wait_correlators(self):
         """Waits for the copies of the last qsg_read_correlators_async;
